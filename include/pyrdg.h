@@ -1,0 +1,186 @@
+/*
+ * pyrdg.h - C ABI of libpyrdg.so: time-explicit discontinuous Galerkin for the
+ * first-order acoustic wave system on meshes of vertex-mapped pyramids, after
+ * Chan & Warburton, "Orthogonal bases for vertex-mapped pyramids".
+ *
+ * What one call computes (Sec. 4.3, rho = kappa = 1, so c = 1 and
+ * tau_p = tau_u = tau): for every element K, with the semi-nodal basis of
+ * Lemma 3 and the cubature of Sec. 4.1,
+ *     M dp/dt   = -( sum_m S^m u_m + L^f F_p ),
+ *     M du_m/dt = -( S^m p          + L^f F_{u_m} ),
+ *     F_p = 1/2 (n.[[u]] - tau [[p]]),   F_u = 1/2 n ([[p]] - tau n.[[u]]),
+ * [[q]] = q+ - q-. M is diagonal in the semi-nodal basis (Lemma 3):
+ *     M_{ijk,ijk} = J(a_i^k, b_j^k) w_i^k w_j^k C_k,  C_k = 2/(2k+3),
+ * and is applied as that diagonal; no per-element matrix is stored or inverted.
+ * Time stepping is the 5-stage 2N-storage RK4 of Carpenter and Kennedy that
+ * Sec. 4.1 cites (Alg. 3 of Sec. 4.2 is its stage update).
+ *
+ * Conventions shared by every call:
+ *  - Reference pyramid (Sec. 2): r, s in [-1, -t], t in [-1, 1]; collapsed
+ *    coordinates a, b, c in [-1, 1] with r = (1+a)(1-c)/2 - 1,
+ *    s = (1+b)(1-c)/2 - 1, t = c.
+ *  - Element vertices (EToV row, 0-based into `vertices`): v1..v4 the base
+ *    quadrilateral with (v2-v1) x (v4-v1) pointing toward the apex v5, v3
+ *    opposite v1 (the images of (-1,-1,-1), (1,-1,-1), (1,1,-1), (-1,1,-1),
+ *    (-1,-1,1)).
+ *  - State layout: row-major [K][4][Np], fields (p, u, v, w), Np =
+ *    (N+1)(N+2)(2N+3)/6 coefficients of the semi-nodal basis per field, in
+ *    the order n = k(k+1)(2k+1)/6 + j(k+1) + i for phi_ijk =
+ *    l_i^k(a) l_j^k(b) ((1-c)/2)^k P_{N-k}^{(2k+3,0)}(c), l^k the Lagrange
+ *    polynomials at the (k+1) Gauss-Legendre points. Element type is double
+ *    for PYR_DG_F64 handles and float for PYR_DG_F32 handles.
+ *  - Errors: every int-returning call returns PYR_DG_OK (0) or a negative
+ *    code; pyr_dg_last_error() then gives a message (thread-local). No C++
+ *    exception crosses this boundary. There is no CPU fallback: without a
+ *    usable CUDA device, calls that compute return PYR_DG_ERR_CUDA.
+ *  - Streams: work is enqueued on opts.stream (a cudaStream_t; NULL means the
+ *    legacy default stream). Calls that return host data synchronise that
+ *    stream; the others return once the work is enqueued.
+ */
+#ifndef PYRDG_H
+#define PYRDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PYR_DG_OK = 0,
+  PYR_DG_ERR_BAD_ARG = -1,        /* null pointer, size out of range, unknown enum */
+  PYR_DG_ERR_BAD_MESH = -2,       /* J <= 0, vertex index out of range, non-conforming face */
+  PYR_DG_ERR_UNSUPPORTED_N = -3,  /* N outside [PYR_DG_MIN_N, PYR_DG_MAX_N] */
+  PYR_DG_ERR_CUDA = -4,           /* CUDA runtime error (message has the CUDA string) */
+  PYR_DG_ERR_NO_MEMORY = -5       /* host or device allocation failed */
+};
+
+enum { PYR_DG_MIN_N = 1, PYR_DG_MAX_N = 7 };
+enum { PYR_DG_F64 = 0, PYR_DG_F32 = 1 };
+enum { PYR_DG_BC_WALL = 0, PYR_DG_BC_FREE = 1 };
+enum { PYR_DG_HOST = 0, PYR_DG_DEVICE = 1 };
+
+typedef struct pyr_dg pyr_dg; /* opaque handle, owned by the library */
+
+typedef struct pyr_dg_opts {
+  int precision;  /* PYR_DG_F64 (state and arithmetic in double) or PYR_DG_F32
+                     (state and stage arithmetic in float; geometry and the
+                     error norm still in double) */
+  int bc;         /* PYR_DG_BC_WALL: rigid wall n.u = 0 (mirror p+ = p-,
+                     u+ = u- - 2(n.u-)n); PYR_DG_BC_FREE: free surface p = 0
+                     of Sec. 4.3 (p+ = -p-, u+ = u-) */
+  double tau;     /* flux penalty of Sec. 4.3: 1 = upwind, 0 = central; >= 0 */
+  void* stream;   /* cudaStream_t for all work of this handle; NULL = default */
+  int device;     /* CUDA device ordinal; -1 = the calling thread's current device */
+} pyr_dg_opts;
+
+/* Fill *opts with: F64, wall, tau = 1, stream NULL, device -1. */
+void pyr_dg_default_opts(pyr_dg_opts* opts);
+
+/* Build a solver for one mesh (Sec. 2 vertex maps, Sec. 4.1 cubature).
+ * vertices: host, Nv x 3 doubles, row-major (copied).
+ * EToV:     host, K x 5 int32 indices into vertices (copied), order as above.
+ * N:        polynomial degree, PYR_DG_MIN_N..PYR_DG_MAX_N.
+ * opts:     may be NULL for the defaults.
+ * On success *out owns device memory for the state, the LSRK residual, face
+ * traces, per-element geometric factors, the mass diagonal and the face
+ * connectivity; the state is zero and the time is 0. Faces are matched by
+ * their vertex sets; every shared face must carry coincident cubature
+ * points (conforming mesh), else PYR_DG_ERR_BAD_MESH. Unshared faces take
+ * the boundary condition. Synchronises the stream. */
+int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_t K, int N,
+                 const pyr_dg_opts* opts, pyr_dg** out);
+
+/* Sizes of a handle: elements K, degree N, coefficients per field Np,
+ * face cubature points per element Nfc = 5(N+1)^2, precision. Any pointer may be NULL. */
+int pyr_dg_info(const pyr_dg* h, int64_t* K, int* N, int* Np, int* Nfc, int* precision);
+
+/* L2 projection (volume rule of Sec. 4.1, diagonal mass of Lemma 3) of the
+ * exact standing wave at time t0 into the state; sets the time to t0 and
+ * zeroes the LSRK residual. 'wall': p = cos(pi x)cos(pi y)cos(pi z)cos(sqrt3 pi t),
+ * u = sin(pi x)cos(pi y)cos(pi z)sin(sqrt3 pi t)/sqrt3 (cyclic), for [0,1]^3;
+ * 'free': the resonant cavity of Sec. 4.3 on [-1,1]^3. Asynchronous. */
+int pyr_dg_project(pyr_dg* h, double t0);
+
+/* Copy a state in (set) or out (get). q: K*4*Np elements of the handle's
+ * type, layout above; `where` = PYR_DG_HOST or PYR_DG_DEVICE says where q
+ * lives. set_state also sets the time to t and zeroes the LSRK residual.
+ * Both synchronise the stream. */
+int pyr_dg_set_state(pyr_dg* h, const void* q, int where, double t);
+int pyr_dg_get_state(pyr_dg* h, void* q, int where);
+
+/* Right-hand side dU/dt = -M^{-1}(volume + surface terms) of the state q
+ * (device pointer, K*4*Np of the handle's type) into rhs (device pointer,
+ * same size, must not alias q). Uses the handle's trace buffer as scratch;
+ * does not touch the handle's own state. Asynchronous. */
+int pyr_dg_rhs(pyr_dg* h, const void* q_dev, void* rhs_dev);
+
+/* Advance the handle's state nsteps LSRK4 steps of size dt (> 0); each step
+ * is 5 stages, each stage one trace launch and one fused
+ * volume + flux + lift + M^{-1} + update launch. Advances the time by
+ * nsteps*dt. Asynchronous. */
+int pyr_dg_step(pyr_dg* h, int nsteps, double dt);
+
+/* L2 error of the state against the exact standing wave at the current time,
+ * integrated in double with (N+3)-point rules (Gauss-Legendre in a, b,
+ * Gauss-Jacobi (2,0) in c), over all four fields; l2_rel divides by the L2
+ * norm of the exact solution. Either pointer may be NULL. Synchronises. */
+int pyr_dg_error(pyr_dg* h, double* l2_abs, double* l2_rel);
+
+/* Time step dt = cfl / (C_N max_K |dK|/|K|), C_N = 2(N+1)(N+3)/3, the
+ * spectral-radius fit of Sec. 4.3. Synchronises. */
+int pyr_dg_dt_cfl(pyr_dg* h, double cfl, double* dt);
+
+/* Current simulation time of the handle. */
+int pyr_dg_time(const pyr_dg* h, double* t);
+
+/* Wait for all work enqueued by this handle. */
+int pyr_dg_sync(pyr_dg* h);
+
+/* Per-kernel timing of pyr_dg_step: with enable != 0, every stage kernel that
+ * pyr_dg_step launches is bracketed by CUDA events on the handle's stream
+ * (a few microseconds of overhead per launch); enable = 0 turns it off. Either
+ * call discards what was recorded before. */
+int pyr_dg_profile(pyr_dg* h, int enable);
+
+/* Totals since the last pyr_dg_profile call: device milliseconds and launch
+ * counts of the trace kernel and of the fused volume/flux/lift/M^{-1}/update
+ * kernel. Synchronises the stream. Any pointer may be NULL. */
+int pyr_dg_profile_read(pyr_dg* h, double* trace_ms, int64_t* trace_launches, double* rhs_ms,
+                        int64_t* rhs_launches);
+
+/* Free the handle and its device memory (synchronises first). NULL is a no-op. */
+void pyr_dg_destroy(pyr_dg* h);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* pyr_dg_last_error(void);
+
+/* ---- host-side builder queries (no GPU needed; used to test the builder) ---- */
+
+/* n-point Gauss-Jacobi rule for weight (1-x)^alpha (1+x)^beta on [-1,1]
+ * (Newton iteration on P_n^{(alpha,beta)}), nodes ascending into x[n],
+ * weights into w[n]. 1 <= n <= 64, alpha, beta > -1. */
+int pyr_dg_host_gauss_jacobi(int n, double alpha, double beta, double* x, double* w);
+
+/* Face connectivity the setup would build, without a GPU. mapP: host,
+ * K*5*(N+1)^2 int64; entry (e*Nfc + g) is the global face-point index
+ * (e'*Nfc + g') matched to point g of element e, or e*Nfc + g itself on a
+ * boundary face. Face-point order per element: face 0 base (a_p, b_q),
+ * g = p + (N+1) q; faces 1..4 = {b=-1, a=+1, b=+1, a=-1} at (x_e, c_m),
+ * g = f(N+1)^2 + e + (N+1) m with x_e the Gauss-Legendre coordinate along the
+ * base edge and c_m the Gauss-Jacobi (1,0) coordinate toward the apex.
+ * nboundary (may be NULL) receives the number of boundary faces. */
+int pyr_dg_host_connectivity(const double* vertices, int64_t Nv, const int32_t* EToV, int64_t K, int N,
+                             int64_t* mapP, int64_t* nboundary);
+
+/* Measured FMA throughput of this GPU in TFLOP/s (2 flops per FMA) for
+ * precision PYR_DG_F64 or PYR_DG_F32: a register-only kernel of independent
+ * FMA chains over every SM, timed with CUDA events. Synchronises the
+ * default stream; used as the ALU roofline peak. */
+int pyr_dg_fma_peak(int precision, double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PYRDG_H */

@@ -169,9 +169,10 @@ class PyramidDG:
                 raise ValueError("non-positive Jacobian at a volume cubature point")
             self.J[sl] = J
             self.X[sl] = X
-            Dphys = np.einsum("kqdm,qdn->kqmn", inv, dref)  # d psi_n / d x_m
-            self.M[sl] = np.einsum("q,kq,qi,qj->kij", w, J, V, V)
-            self.S[sl] = np.einsum("q,kq,qi,kqmj->kmij", w, J, V, Dphys)
+            Dphys = np.einsum("kqdm,qdn->kqmn", inv, dref, optimize=True)  # d psi_n / d x_m
+            wJ = w[None, :] * J
+            self.M[sl] = np.einsum("kq,qi,qj->kij", wJ, V, V, optimize=True)
+            self.S[sl] = np.einsum("kq,qi,kqmj->kmij", wJ, V, Dphys, optimize=True)
         self.Minv = np.linalg.inv(self.M)
 
         # faces

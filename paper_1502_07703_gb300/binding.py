@@ -1,0 +1,261 @@
+"""Thin ctypes binding of libpyrdg.so (C ABI in include/pyrdg.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels. PyTorch supplies device memory (``rhs``, device-side state
+copies) and the default stream. Loading fails loudly when the library has not
+been built; there is no Python or CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpyrdg.so")
+
+PYR_DG_F64, PYR_DG_F32 = 0, 1
+PYR_DG_BC_WALL, PYR_DG_BC_FREE = 0, 1
+PYR_DG_HOST, PYR_DG_DEVICE = 0, 1
+ERRORS = {-1: "BAD_ARG", -2: "BAD_MESH", -3: "UNSUPPORTED_N", -4: "CUDA", -5: "NO_MEMORY"}
+
+_lib = None
+
+
+class PyrDGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("bc", ctypes.c_int),
+        ("tau", ctypes.c_double),
+        ("stream", ctypes.c_void_p),
+        ("device", ctypes.c_int),
+    ]
+
+
+_c_dp = ctypes.POINTER(ctypes.c_double)
+_c_ip = ctypes.POINTER(ctypes.c_int)
+_c_i64p = ctypes.POINTER(ctypes.c_int64)
+_c_i32p = ctypes.POINTER(ctypes.c_int32)
+_c_h = ctypes.c_void_p
+
+_SIGNATURES = {
+    "pyr_dg_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "pyr_dg_setup": (ctypes.c_int, [_c_dp, ctypes.c_int64, _c_i32p, ctypes.c_int64, ctypes.c_int,
+                                    ctypes.POINTER(Opts), ctypes.POINTER(_c_h)]),
+    "pyr_dg_info": (ctypes.c_int, [_c_h, _c_i64p, _c_ip, _c_ip, _c_ip, _c_ip]),
+    "pyr_dg_project": (ctypes.c_int, [_c_h, ctypes.c_double]),
+    "pyr_dg_set_state": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
+    "pyr_dg_get_state": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_int]),
+    "pyr_dg_rhs": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_void_p]),
+    "pyr_dg_step": (ctypes.c_int, [_c_h, ctypes.c_int, ctypes.c_double]),
+    "pyr_dg_error": (ctypes.c_int, [_c_h, _c_dp, _c_dp]),
+    "pyr_dg_dt_cfl": (ctypes.c_int, [_c_h, ctypes.c_double, _c_dp]),
+    "pyr_dg_time": (ctypes.c_int, [_c_h, _c_dp]),
+    "pyr_dg_sync": (ctypes.c_int, [_c_h]),
+    "pyr_dg_destroy": (None, [_c_h]),
+    "pyr_dg_last_error": (ctypes.c_char_p, []),
+    "pyr_dg_host_gauss_jacobi": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, ctypes.c_double, _c_dp, _c_dp]),
+    "pyr_dg_host_connectivity": (ctypes.c_int, [_c_dp, ctypes.c_int64, _c_i32p, ctypes.c_int64, ctypes.c_int,
+                                                _c_i64p, _c_i64p]),
+    "pyr_dg_fma_peak": (ctypes.c_int, [ctypes.c_int, _c_dp]),
+    "pyr_dg_profile": (ctypes.c_int, [_c_h, ctypes.c_int]),
+    "pyr_dg_profile_read": (ctypes.c_int, [_c_h, _c_dp, _c_i64p, _c_dp, _c_i64p]),
+}
+
+
+def lib():
+    """Load libpyrdg.so (once) and declare its signatures. Raises if it is not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with paper_1502_07703_gb300.build.build() "
+                "(or __graft_entry__.build()); there is no fallback implementation")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise PyrDGError(rc, lib().pyr_dg_last_error().decode())
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def gauss_jacobi(n, alpha, beta):
+    """The library's host Gauss-Jacobi rule: (nodes, weights)."""
+    x = np.empty(n)
+    w = np.empty(n)
+    _check(lib().pyr_dg_host_gauss_jacobi(n, alpha, beta, _ptr(x, ctypes.c_double), _ptr(w, ctypes.c_double)))
+    return x, w
+
+
+def connectivity(vertices, EToV, N):
+    """The library's host face connectivity: (mapP (K*Nfc,) int64, number of boundary faces)."""
+    V = np.ascontiguousarray(vertices, dtype=np.float64)
+    E = np.ascontiguousarray(EToV, dtype=np.int32)
+    K = E.shape[0]
+    mapP = np.empty(K * 5 * (N + 1) ** 2, dtype=np.int64)
+    nb = ctypes.c_int64(0)
+    _check(lib().pyr_dg_host_connectivity(_ptr(V, ctypes.c_double), V.shape[0], _ptr(E, ctypes.c_int32), K, N,
+                                          _ptr(mapP, ctypes.c_int64), ctypes.byref(nb)))
+    return mapP, nb.value
+
+
+def fma_peak(precision="f64"):
+    """Measured FMA throughput of the current GPU in TFLOP/s."""
+    out = ctypes.c_double(0.0)
+    _check(lib().pyr_dg_fma_peak(PYR_DG_F64 if precision == "f64" else PYR_DG_F32, ctypes.byref(out)))
+    return out.value
+
+
+class Solver:
+    """One mesh advanced by the library. State arrays are (K, 4, Np) in the
+    handle's precision, semi-nodal coefficients (layout in include/pyrdg.h)."""
+
+    def __init__(self, vertices, EToV, N, precision="f64", bc="wall", tau=1.0, stream=None, device=None):
+        import torch
+
+        self._torch = torch
+        V = np.ascontiguousarray(vertices, dtype=np.float64)
+        E = np.ascontiguousarray(EToV, dtype=np.int32)
+        if V.ndim != 2 or V.shape[1] != 3 or E.ndim != 2 or E.shape[1] != 5:
+            raise ValueError("vertices must be (Nv, 3) and EToV (K, 5)")
+        o = Opts()
+        lib().pyr_dg_default_opts(ctypes.byref(o))
+        o.precision = {"f64": PYR_DG_F64, "f32": PYR_DG_F32}[precision]
+        o.bc = {"wall": PYR_DG_BC_WALL, "free": PYR_DG_BC_FREE}[bc]
+        o.tau = float(tau)
+        if device is None:
+            device = torch.cuda.current_device() if torch.cuda.is_available() else 0
+        o.device = int(device)
+        if stream is None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream(device).cuda_stream
+        o.stream = stream
+        h = _c_h()
+        _check(lib().pyr_dg_setup(_ptr(V, ctypes.c_double), V.shape[0], _ptr(E, ctypes.c_int32), E.shape[0], int(N),
+                                  ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.device = device
+        self.precision = precision
+        self.bc = bc
+        self.tau = float(tau)
+        K, n, Np, Nfc, prec = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().pyr_dg_info(h, ctypes.byref(K), ctypes.byref(n), ctypes.byref(Np), ctypes.byref(Nfc),
+                                 ctypes.byref(prec)))
+        self.K, self.N, self.Np, self.Nfc = K.value, n.value, Np.value, Nfc.value
+        self.np_dtype = np.float64 if precision == "f64" else np.float32
+        self.torch_dtype = torch.float64 if precision == "f64" else torch.float32
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pyr_dg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def shape(self):
+        return (self.K, 4, self.Np)
+
+    # -- calls
+    def project(self, t0=0.0):
+        _check(lib().pyr_dg_project(self._h, float(t0)))
+
+    def set_state(self, q, t=0.0):
+        """q: numpy array (host) or torch CUDA tensor (device), shape (K, 4, Np)."""
+        if isinstance(q, np.ndarray):
+            a = np.ascontiguousarray(q, dtype=self.np_dtype).reshape(self.shape)
+            _check(lib().pyr_dg_set_state(self._h, a.ctypes.data, PYR_DG_HOST, float(t)))
+        else:
+            a = q.contiguous().to(self.torch_dtype).reshape(self.shape)
+            self._require_device(a)
+            _check(lib().pyr_dg_set_state(self._h, a.data_ptr(), PYR_DG_DEVICE, float(t)))
+
+    def set_state_host_ptr(self, ptr, t=0.0):
+        """Set the state from a raw host pointer (e.g. a pinned torch tensor's data_ptr())."""
+        _check(lib().pyr_dg_set_state(self._h, ctypes.c_void_p(ptr), PYR_DG_HOST, float(t)))
+
+    def get_state(self, device=False):
+        """Copy of the state: numpy array, or a torch CUDA tensor if device=True."""
+        if device:
+            out = self._torch.empty(self.shape, dtype=self.torch_dtype, device=f"cuda:{self.device}")
+            _check(lib().pyr_dg_get_state(self._h, out.data_ptr(), PYR_DG_DEVICE))
+            return out
+        out = np.empty(self.shape, dtype=self.np_dtype)
+        _check(lib().pyr_dg_get_state(self._h, out.ctypes.data, PYR_DG_HOST))
+        return out
+
+    def rhs(self, q, out=None):
+        """dU/dt of q (torch CUDA tensor (K, 4, Np) of the handle's dtype) into a new or given tensor."""
+        self._require_device(q)
+        q = q.contiguous()
+        if out is None:
+            out = self._torch.empty_like(q)
+        self._require_device(out)
+        _check(lib().pyr_dg_rhs(self._h, q.data_ptr(), out.data_ptr()))
+        return out
+
+    def step(self, nsteps, dt):
+        _check(lib().pyr_dg_step(self._h, int(nsteps), float(dt)))
+
+    def error(self):
+        a, r = ctypes.c_double(), ctypes.c_double()
+        _check(lib().pyr_dg_error(self._h, ctypes.byref(a), ctypes.byref(r)))
+        return a.value, r.value
+
+    def dt_cfl(self, cfl=0.5):
+        dt = ctypes.c_double()
+        _check(lib().pyr_dg_dt_cfl(self._h, float(cfl), ctypes.byref(dt)))
+        return dt.value
+
+    @property
+    def time(self):
+        t = ctypes.c_double()
+        _check(lib().pyr_dg_time(self._h, ctypes.byref(t)))
+        return t.value
+
+    def profile(self, enable=True):
+        """Start (or stop) per-kernel CUDA-event timing of step()."""
+        _check(lib().pyr_dg_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{'trace': (ms, launches), 'rhs': (ms, launches)} since profile() was called."""
+        tm, rm = ctypes.c_double(), ctypes.c_double()
+        tn, rn = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().pyr_dg_profile_read(self._h, ctypes.byref(tm), ctypes.byref(tn), ctypes.byref(rm),
+                                         ctypes.byref(rn)))
+        return {"trace": (tm.value, tn.value), "rhs": (rm.value, rn.value)}
+
+    def sync(self):
+        _check(lib().pyr_dg_sync(self._h))
+
+    def _require_device(self, t):
+        if not (hasattr(t, "is_cuda") and t.is_cuda) or t.dtype != self.torch_dtype or tuple(t.shape) != self.shape:
+            raise ValueError(f"expected a CUDA tensor of shape {self.shape} and dtype {self.torch_dtype}")

@@ -1,0 +1,466 @@
+// C ABI of libpyrdg.so (declared in include/pyrdg.h): handle lifetime, setup
+// (host builder + device geometry), and the per-call launch sequences.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pyrdg.h"
+#include "builder.h"
+#include "launch.h"
+
+namespace pyrdg {
+const Launchers* launchers_n1(int);
+const Launchers* launchers_n2(int);
+const Launchers* launchers_n3(int);
+const Launchers* launchers_n4(int);
+const Launchers* launchers_n5(int);
+const Launchers* launchers_n6(int);
+const Launchers* launchers_n7(int);
+
+const Launchers* get_launchers(int N, int precision) {
+  switch (N) {
+    case 1: return launchers_n1(precision);
+    case 2: return launchers_n2(precision);
+    case 3: return launchers_n3(precision);
+    case 4: return launchers_n4(precision);
+    case 5: return launchers_n5(precision);
+    case 6: return launchers_n6(precision);
+    case 7: return launchers_n7(precision);
+    default: return nullptr;
+  }
+}
+}  // namespace pyrdg
+
+// Carpenter & Kennedy (1994) 5-stage 2N-storage RK4 (cited in Sec. 4.1).
+static const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                               -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+static const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                               2277821191437.0 / 14882151754819.0};
+
+struct pyr_dg {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int N = 0, Np = 0, Nfc = 0, precision = 0, bc = 0;
+  double tau = 1.0;
+  int64_t K = 0;
+  size_t tsize = 8;
+  double t = 0.0;
+  double max_aov = 0.0;
+  int err_blocks = 0;
+  const pyrdg::Launchers* L = nullptr;
+  void *q = nullptr, *res = nullptr, *tr = nullptr, *geo = nullptr, *gface = nullptr, *invM = nullptr,
+       *tab = nullptr;
+  double *tabd = nullptr, *gtab = nullptr, *ev = nullptr, *partial = nullptr;
+  int32_t* mapP = nullptr;
+  // per-kernel event timing of pyr_dg_step (pyr_dg_profile)
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  std::vector<int> event_kind;  // per recorded pair: 0 trace, 1 rhs
+  size_t events_used = 0;
+};
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                    \
+  do {                                                                                    \
+    cudaError_t _e = (expr);                                                              \
+    if (_e != cudaSuccess)                                                                \
+      return fail(PYR_DG_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(_e));      \
+  } while (0)
+
+namespace {
+// Makes the handle's device current for the duration of a call, restoring the caller's.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    int cur = 0;
+    err = cudaGetDevice(&cur);
+    if (err == cudaSuccess && cur != dev) {
+      err = cudaSetDevice(dev);
+      if (err == cudaSuccess) prev = cur;
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Record an event pair slot around the next launch when profiling (kind 0 trace, 1 rhs).
+cudaError_t prof_begin(pyr_dg* h, int kind, size_t* slot) {
+  if (!h->profiling) return cudaSuccess;
+  if (h->events_used + 2 > h->events.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t ev;
+      cudaError_t e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return e;
+      h->events.push_back(ev);
+    }
+  }
+  *slot = h->events_used;
+  h->events_used += 2;
+  h->event_kind.push_back(kind);
+  return cudaEventRecord(h->events[*slot], h->stream);
+}
+
+cudaError_t prof_end(pyr_dg* h, size_t slot) {
+  if (!h->profiling) return cudaSuccess;
+  return cudaEventRecord(h->events[slot + 1], h->stream);
+}
+
+void free_all(pyr_dg* h) {
+  for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
+  h->events.clear();
+  void* ptrs[] = {h->q,    h->res,  h->tr, h->geo,     h->gface, h->invM, h->tab,
+                  h->tabd, h->gtab, h->ev, h->partial, h->mapP};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+}  // namespace
+
+extern "C" {
+
+void pyr_dg_default_opts(pyr_dg_opts* o) {
+  if (!o) return;
+  o->precision = PYR_DG_F64;
+  o->bc = PYR_DG_BC_WALL;
+  o->tau = 1.0;
+  o->stream = nullptr;
+  o->device = -1;
+}
+
+const char* pyr_dg_last_error(void) { return g_err.c_str(); }
+
+int pyr_dg_host_gauss_jacobi(int n, double alpha, double beta, double* x, double* w) {
+  if (!x || !w) return fail(PYR_DG_ERR_BAD_ARG, "null output pointer");
+  if (pyrdg::gauss_jacobi(n, alpha, beta, x, w) != 0)
+    return fail(PYR_DG_ERR_BAD_ARG, "gauss_jacobi: need 1 <= n <= 64 and alpha, beta > -1");
+  return PYR_DG_OK;
+}
+
+int pyr_dg_host_connectivity(const double* vertices, int64_t Nv, const int32_t* EToV, int64_t K, int N,
+                             int64_t* mapP, int64_t* nboundary) {
+  if (!vertices || !EToV || !mapP || Nv < 1 || K < 1) return fail(PYR_DG_ERR_BAD_ARG, "bad connectivity arguments");
+  if (N < PYR_DG_MIN_N || N > PYR_DG_MAX_N) return fail(PYR_DG_ERR_UNSUPPORTED_N, "N = %d unsupported", N);
+  std::vector<int64_t> m;
+  std::string err;
+  const int rc = pyrdg::build_connectivity(vertices, Nv, EToV, K, N, m, nboundary, err);
+  if (rc != 0) return fail(PYR_DG_ERR_BAD_MESH, "%s", err.c_str());
+  std::memcpy(mapP, m.data(), m.size() * sizeof(int64_t));
+  return PYR_DG_OK;
+}
+
+int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_t K, int N, const pyr_dg_opts* opts,
+                 pyr_dg** out) {
+  g_err.clear();
+  if (!out) return fail(PYR_DG_ERR_BAD_ARG, "out is null");
+  *out = nullptr;
+  if (!vertices || !EToV) return fail(PYR_DG_ERR_BAD_ARG, "vertices or EToV is null");
+  if (Nv < 5 || K < 1) return fail(PYR_DG_ERR_BAD_ARG, "need Nv >= 5 and K >= 1 (got %lld, %lld)", (long long)Nv,
+                                   (long long)K);
+  if (K > 0x7fffffffLL) return fail(PYR_DG_ERR_BAD_ARG, "K = %lld exceeds the grid limit", (long long)K);
+  if (N < PYR_DG_MIN_N || N > PYR_DG_MAX_N)
+    return fail(PYR_DG_ERR_UNSUPPORTED_N, "N = %d outside [%d, %d]", N, PYR_DG_MIN_N, PYR_DG_MAX_N);
+  pyr_dg_opts o;
+  pyr_dg_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.precision != PYR_DG_F64 && o.precision != PYR_DG_F32) return fail(PYR_DG_ERR_BAD_ARG, "unknown precision");
+  if (o.bc != PYR_DG_BC_WALL && o.bc != PYR_DG_BC_FREE) return fail(PYR_DG_ERR_BAD_ARG, "unknown bc");
+  if (!(o.tau >= 0.0) || !std::isfinite(o.tau)) return fail(PYR_DG_ERR_BAD_ARG, "tau must be finite and >= 0");
+  const int n1 = N + 1, n2 = n1 * n1, Nfc = 5 * n2, Np = pyrdg::num_modes(N);
+  if (K * (int64_t)Nfc > 0x7fffffffLL) return fail(PYR_DG_ERR_BAD_ARG, "K * Nfc exceeds int32 face indexing");
+
+  // ---- host builder
+  pyrdg::RefTables T;
+  if (pyrdg::build_tables(N, T) != 0) return fail(PYR_DG_ERR_UNSUPPORTED_N, "table build failed for N = %d", N);
+  std::vector<int64_t> map64;
+  std::string err;
+  int64_t nbnd = 0;
+  if (pyrdg::build_connectivity(vertices, Nv, EToV, K, N, map64, &nbnd, err) != 0)
+    return fail(PYR_DG_ERR_BAD_MESH, "%s", err.c_str());
+  std::vector<double> ev((size_t)K * 15);
+  const pyrdg::GeoLayout G(N);
+  double max_aov = 0.0;
+  for (int64_t e = 0; e < K; ++e) {
+    double* v = &ev[(size_t)e * 15];
+    for (int m = 0; m < 15; ++m) v[m] = vertices[(int64_t)EToV[e * 5 + m / 3] * 3 + m % 3];
+    // J is bilinear in (a, b) (Lemma 1): positive everywhere iff positive at the 4 corners
+    for (int c = 0; c < 4; ++c) {
+      const double J = pyrdg::jacobian_ab(v, (c & 1) ? 1.0 : -1.0, (c & 2) ? 1.0 : -1.0);
+      if (!(J > 0.0))
+        return fail(PYR_DG_ERR_BAD_MESH, "element %lld has J = %g <= 0 at a base corner (vertex order or inverted)",
+                    (long long)e, J);
+    }
+    const double aov = pyrdg::area_over_volume(v, &T.geo[G.XG], &T.geo[G.WG], n1);
+    if (aov > max_aov) max_aov = aov;
+  }
+  std::vector<int32_t> map32((size_t)K * Nfc);
+  for (size_t g = 0; g < map32.size(); ++g) map32[g] = (int32_t)map64[g];
+
+  pyr_dg* h = new (std::nothrow) pyr_dg();
+  if (!h) return fail(PYR_DG_ERR_NO_MEMORY, "host allocation failed");
+  h->N = N;
+  h->Np = Np;
+  h->Nfc = Nfc;
+  h->K = K;
+  h->precision = o.precision;
+  h->bc = o.bc;
+  h->tau = o.tau;
+  h->tsize = o.precision == PYR_DG_F64 ? 8 : 4;
+  h->stream = (cudaStream_t)o.stream;
+  h->max_aov = max_aov;
+  h->L = pyrdg::get_launchers(N, o.precision);
+  if (o.device >= 0) {
+    h->device = o.device;
+  } else if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return fail(PYR_DG_ERR_CUDA, "no CUDA device available");
+  }
+  DeviceGuard guard(h->device);
+  if (guard.err != cudaSuccess) {
+    delete h;
+    return fail(PYR_DG_ERR_CUDA, "cannot select device %d: %s", h->device, cudaGetErrorString(guard.err));
+  }
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  h->err_blocks = (int)std::min<int64_t>(K, (int64_t)(nsm > 0 ? nsm : 1) * 4);
+
+  const size_t ts = h->tsize;
+  const size_t stateB = (size_t)K * 4 * Np * ts;
+  const pyrdg::TabLayout TL(N);
+  struct Alloc {
+    void** p;
+    size_t bytes;
+  } allocs[] = {
+      {&h->q, stateB},
+      {&h->res, stateB},
+      {&h->tr, (size_t)K * Nfc * 4 * ts},
+      {&h->geo, (size_t)K * n2 * 9 * ts},
+      {&h->gface, (size_t)K * (16 + 4 * n2) * ts},
+      {&h->invM, (size_t)K * Np * ts},
+      {&h->tab, (size_t)TL.size * ts},
+      {(void**)&h->tabd, (size_t)TL.size * 8},
+      {(void**)&h->gtab, (size_t)G.size * 8},
+      {(void**)&h->ev, (size_t)K * 15 * 8},
+      {(void**)&h->partial, (size_t)h->err_blocks * 2 * 8},
+      {(void**)&h->mapP, (size_t)K * Nfc * 4},
+  };
+  for (auto& a : allocs) {
+    cudaError_t e = cudaMalloc(a.p, a.bytes);
+    if (e != cudaSuccess) {
+      free_all(h);
+      delete h;
+      return fail(e == cudaErrorMemoryAllocation ? PYR_DG_ERR_NO_MEMORY : PYR_DG_ERR_CUDA,
+                  "cudaMalloc(%zu bytes): %s", a.bytes, cudaGetErrorString(e));
+    }
+  }
+  std::vector<float> tabf;
+  const void* tabsrc = T.tab.data();
+  if (ts == 4) {
+    tabf.assign(T.tab.begin(), T.tab.end());
+    tabsrc = tabf.data();
+  }
+  cudaError_t e = cudaSuccess;
+  cudaStream_t s = h->stream;
+  if (e == cudaSuccess) e = h->L->prepare();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->tab, tabsrc, (size_t)TL.size * ts, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->tabd, T.tab.data(), (size_t)TL.size * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->gtab, T.geo.data(), (size_t)G.size * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->ev, ev.data(), ev.size() * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->mapP, map32.data(), map32.size() * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->q, 0, stateB, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->res, 0, stateB, s);
+  if (e == cudaSuccess) {
+    h->L->geom(K, h->ev, h->gtab, h->geo, h->gface, h->invM, s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return fail(PYR_DG_ERR_CUDA, "setup: %s", cudaGetErrorString(e));
+  }
+  *out = h;
+  return PYR_DG_OK;
+}
+
+int pyr_dg_info(const pyr_dg* h, int64_t* K, int* N, int* Np, int* Nfc, int* precision) {
+  if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
+  if (K) *K = h->K;
+  if (N) *N = h->N;
+  if (Np) *Np = h->Np;
+  if (Nfc) *Nfc = h->Nfc;
+  if (precision) *precision = h->precision;
+  return PYR_DG_OK;
+}
+
+int pyr_dg_project(pyr_dg* h, double t0) {
+  if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
+  if (!std::isfinite(t0)) return fail(PYR_DG_ERR_BAD_ARG, "t0 must be finite");
+  DeviceGuard g(h->device);
+  CUDA_TRY(g.err);
+  h->L->project(h->K, h->ev, h->gtab, h->tabd, h->bc, t0, h->q, h->stream);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemsetAsync(h->res, 0, (size_t)h->K * 4 * h->Np * h->tsize, h->stream));
+  h->t = t0;
+  return PYR_DG_OK;
+}
+
+int pyr_dg_set_state(pyr_dg* h, const void* q, int where, double t) {
+  if (!h || !q) return fail(PYR_DG_ERR_BAD_ARG, "null argument");
+  if (where != PYR_DG_HOST && where != PYR_DG_DEVICE) return fail(PYR_DG_ERR_BAD_ARG, "bad `where`");
+  DeviceGuard g(h->device);
+  CUDA_TRY(g.err);
+  const size_t bytes = (size_t)h->K * 4 * h->Np * h->tsize;
+  CUDA_TRY(cudaMemcpyAsync(h->q, q, bytes, where == PYR_DG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                           h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->res, 0, bytes, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  h->t = t;
+  return PYR_DG_OK;
+}
+
+int pyr_dg_get_state(pyr_dg* h, void* q, int where) {
+  if (!h || !q) return fail(PYR_DG_ERR_BAD_ARG, "null argument");
+  if (where != PYR_DG_HOST && where != PYR_DG_DEVICE) return fail(PYR_DG_ERR_BAD_ARG, "bad `where`");
+  DeviceGuard g(h->device);
+  CUDA_TRY(g.err);
+  const size_t bytes = (size_t)h->K * 4 * h->Np * h->tsize;
+  CUDA_TRY(cudaMemcpyAsync(q, h->q, bytes, where == PYR_DG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                           h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return PYR_DG_OK;
+}
+
+int pyr_dg_rhs(pyr_dg* h, const void* q_dev, void* rhs_dev) {
+  if (!h || !q_dev || !rhs_dev) return fail(PYR_DG_ERR_BAD_ARG, "null argument");
+  if (q_dev == rhs_dev) return fail(PYR_DG_ERR_BAD_ARG, "rhs must not alias q");
+  DeviceGuard g(h->device);
+  CUDA_TRY(g.err);
+  h->L->trace(h->K, q_dev, h->tab, h->tr, h->stream);
+  h->L->rhs_out(h->K, q_dev, rhs_dev, h->tr, h->mapP, h->geo, h->gface, h->invM, h->tab, h->bc, h->tau, h->stream);
+  CUDA_TRY(cudaGetLastError());
+  return PYR_DG_OK;
+}
+
+int pyr_dg_step(pyr_dg* h, int nsteps, double dt) {
+  if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
+  if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(PYR_DG_ERR_BAD_ARG, "need nsteps >= 0, dt > 0");
+  DeviceGuard g(h->device);
+  CUDA_TRY(g.err);
+  for (int n = 0; n < nsteps; ++n) {
+    for (int s = 0; s < 5; ++s) {
+      size_t slot = 0;
+      CUDA_TRY(prof_begin(h, 0, &slot));
+      h->L->trace(h->K, h->q, h->tab, h->tr, h->stream);
+      CUDA_TRY(prof_end(h, slot));
+      CUDA_TRY(prof_begin(h, 1, &slot));
+      h->L->rhs_update(h->K, h->q, h->res, h->tr, h->mapP, h->geo, h->gface, h->invM, h->tab, h->bc, h->tau, kRkA[s],
+                       kRkB[s], dt, h->stream);
+      CUDA_TRY(prof_end(h, slot));
+    }
+  }
+  CUDA_TRY(cudaGetLastError());
+  h->t += nsteps * dt;
+  return PYR_DG_OK;
+}
+
+int pyr_dg_error(pyr_dg* h, double* l2_abs, double* l2_rel) {
+  if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
+  DeviceGuard g(h->device);
+  CUDA_TRY(g.err);
+  h->L->error(h->K, h->q, h->ev, h->gtab, h->bc, h->t, h->partial, h->err_blocks, h->stream);
+  CUDA_TRY(cudaGetLastError());
+  std::vector<double> part((size_t)h->err_blocks * 2);
+  CUDA_TRY(cudaMemcpyAsync(part.data(), h->partial, part.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  double e2 = 0.0, n2 = 0.0;
+  for (int b = 0; b < h->err_blocks; ++b) {
+    e2 += part[2 * b];
+    n2 += part[2 * b + 1];
+  }
+  if (l2_abs) *l2_abs = std::sqrt(e2);
+  if (l2_rel) *l2_rel = n2 > 0 ? std::sqrt(e2 / n2) : std::sqrt(e2);
+  return PYR_DG_OK;
+}
+
+int pyr_dg_dt_cfl(pyr_dg* h, double cfl, double* dt) {
+  if (!h || !dt) return fail(PYR_DG_ERR_BAD_ARG, "null argument");
+  if (!(cfl > 0.0)) return fail(PYR_DG_ERR_BAD_ARG, "cfl must be > 0");
+  const double CN = 2.0 * (h->N + 1) * (h->N + 3) / 3.0;
+  *dt = cfl / (CN * h->max_aov);
+  return PYR_DG_OK;
+}
+
+int pyr_dg_time(const pyr_dg* h, double* t) {
+  if (!h || !t) return fail(PYR_DG_ERR_BAD_ARG, "null argument");
+  *t = h->t;
+  return PYR_DG_OK;
+}
+
+int pyr_dg_sync(pyr_dg* h) {
+  if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
+  DeviceGuard g(h->device);
+  CUDA_TRY(g.err);
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return PYR_DG_OK;
+}
+
+int pyr_dg_profile(pyr_dg* h, int enable) {
+  if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
+  DeviceGuard g(h->device);
+  CUDA_TRY(g.err);
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  h->profiling = enable != 0;
+  h->events_used = 0;
+  h->event_kind.clear();
+  return PYR_DG_OK;
+}
+
+int pyr_dg_profile_read(pyr_dg* h, double* trace_ms, int64_t* trace_launches, double* rhs_ms,
+                        int64_t* rhs_launches) {
+  if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
+  DeviceGuard g(h->device);
+  CUDA_TRY(g.err);
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  double ms[2] = {0.0, 0.0};
+  int64_t cnt[2] = {0, 0};
+  for (size_t p = 0; p < h->event_kind.size(); ++p) {
+    float t = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&t, h->events[2 * p], h->events[2 * p + 1]));
+    ms[h->event_kind[p]] += t;
+    cnt[h->event_kind[p]] += 1;
+  }
+  if (trace_ms) *trace_ms = ms[0];
+  if (trace_launches) *trace_launches = cnt[0];
+  if (rhs_ms) *rhs_ms = ms[1];
+  if (rhs_launches) *rhs_launches = cnt[1];
+  return PYR_DG_OK;
+}
+
+void pyr_dg_destroy(pyr_dg* h) {
+  if (!h) return;
+  DeviceGuard g(h->device);
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+}
+
+}  // extern "C"

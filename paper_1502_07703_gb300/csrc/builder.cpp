@@ -1,0 +1,400 @@
+// Host FP64 builder: Gauss rules, semi-nodal reference tables, vertex-map
+// geometry checks and face connectivity. Everything here runs once per setup.
+#include "builder.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+namespace pyrdg {
+
+// ---------------------------------------------------------------- polynomials
+// Jacobi P_n^{(al,be)} with P_n(1) = binom(n+al, n), three-term recurrence.
+double jacobi_p(int n, double al, double be, double x) {
+  if (n == 0) return 1.0;
+  double pm = 1.0;
+  double p = 0.5 * (al - be + (al + be + 2.0) * x);
+  for (int m = 2; m <= n; ++m) {
+    const double s = 2.0 * m + al + be;
+    const double c1 = 2.0 * m * (m + al + be) * (s - 2.0);
+    const double c2 = (s - 1.0) * (al * al - be * be);
+    const double c3 = (s - 2.0) * (s - 1.0) * s;
+    const double c4 = 2.0 * (m + al - 1.0) * (m + be - 1.0) * s;
+    const double pn = ((c2 + c3 * x) * p - c4 * pm) / c1;
+    pm = p;
+    p = pn;
+  }
+  return p;
+}
+
+double jacobi_dp(int n, double al, double be, double x) {
+  if (n == 0) return 0.0;
+  return 0.5 * (n + al + be + 1.0) * jacobi_p(n - 1, al + 1.0, be + 1.0, x);
+}
+
+// Gauss-Jacobi nodes by Newton iteration with deflation from Chebyshev
+// starting guesses (Karniadakis & Sherwin's zero finder), then the weights
+// w_i = 2^{al+be+1} G(n+al+1) G(n+be+1) / (G(n+al+be+1) n!) / ((1-x^2) P_n'(x)^2).
+int gauss_jacobi(int n, double al, double be, double* x, double* w) {
+  if (n < 1 || n > 64 || !(al > -1.0) || !(be > -1.0)) return -1;
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < n; ++k) {
+    double r = -std::cos((2.0 * k + 1.0) * pi / (2.0 * n));
+    if (k > 0) r = 0.5 * (r + x[k - 1]);
+    for (int it = 0; it < 200; ++it) {
+      double s = 0.0;
+      for (int i = 0; i < k; ++i) s += 1.0 / (r - x[i]);
+      const double p = jacobi_p(n, al, be, r);
+      const double dp = jacobi_dp(n, al, be, r);
+      const double delta = -p / (dp - s * p);
+      r += delta;
+      if (std::fabs(delta) < 1e-16) break;
+    }
+    x[k] = r;
+  }
+  for (int k = 0; k < n; ++k) {  // polish without deflation
+    double r = x[k];
+    for (int it = 0; it < 3; ++it) r -= jacobi_p(n, al, be, r) / jacobi_dp(n, al, be, r);
+    x[k] = r;
+  }
+  std::sort(x, x + n);
+  const double lc = (al + be + 1.0) * std::log(2.0) + std::lgamma(n + al + 1.0) + std::lgamma(n + be + 1.0) -
+                    std::lgamma(n + al + be + 1.0) - std::lgamma(n + 1.0);
+  const double C = std::exp(lc);
+  for (int k = 0; k < n; ++k) {
+    const double dp = jacobi_dp(n, al, be, x[k]);
+    w[k] = C / ((1.0 - x[k] * x[k]) * dp * dp);
+  }
+  return 0;
+}
+
+// Lagrange basis on `nodes` (size n) and its derivative at x.
+static void lagrange(const double* nodes, int n, double x, double* L, double* dL) {
+  for (int i = 0; i < n; ++i) {
+    double v = 1.0;
+    for (int m = 0; m < n; ++m)
+      if (m != i) v *= (x - nodes[m]) / (nodes[i] - nodes[m]);
+    L[i] = v;
+    double d = 0.0;
+    for (int l = 0; l < n; ++l) {
+      if (l == i) continue;
+      double t = 1.0 / (nodes[i] - nodes[l]);
+      for (int m = 0; m < n; ++m)
+        if (m != i && m != l) t *= (x - nodes[m]) / (nodes[i] - nodes[m]);
+      d += t;
+    }
+    dL[i] = d;
+  }
+}
+
+// G_k(c) = ((1-c)/2)^k P_{N-k}^{(2k+3,0)}(c), its derivative, and
+// H_k(c) = ((1-c)/2)^{k-1} P_{N-k}^{(2k+3,0)}(c) = 2/(1-c) G_k(c) (0 for k = 0).
+static void cfun(int N, int k, double c, double* G, double* dG, double* H) {
+  const double h = 0.5 * (1.0 - c);
+  const double P = jacobi_p(N - k, 2.0 * k + 3.0, 0.0, c);
+  const double dP = jacobi_dp(N - k, 2.0 * k + 3.0, 0.0, c);
+  const double hk = std::pow(h, k);
+  const double hk1 = k >= 1 ? std::pow(h, k - 1) : 0.0;
+  if (G) *G = hk * P;
+  if (dG) *dG = -0.5 * k * hk1 * P + hk * dP;
+  if (H) *H = hk1 * P;
+}
+
+int build_tables(int N, RefTables& t) {
+  if (N < 1 || N > 7) return -1;
+  const int n1 = N + 1, P3 = N + 3, Q = N + 3, nrow = tri_num(n1), Np = num_modes(N);
+  const TabLayout L(N);
+  const GeoLayout G(N);
+  t.N = N;
+  t.tab.assign(L.size, 0.0);
+  t.geo.assign(G.size, 0.0);
+  std::vector<double> xg(n1), wg(n1), xc(n1), wc(n1), xf(n1), wf(n1);
+  gauss_jacobi(n1, 0.0, 0.0, xg.data(), wg.data());
+  gauss_jacobi(n1, 2.0, 0.0, xc.data(), wc.data());
+  gauss_jacobi(n1, 1.0, 0.0, xf.data(), wf.data());
+  std::vector<double> xe(P3);
+  for (int p = 0; p < n1; ++p) xe[p] = xg[p];
+  xe[n1] = -1.0;
+  xe[n1 + 1] = 1.0;
+
+  // C_k = int ((1-c)/2)^{2k+2} (P_{N-k}^{(2k+3,0)})^2 dc by an exact Gauss-Legendre rule
+  std::vector<double> xh(N + 3), wh(N + 3), Ck(n1);
+  gauss_jacobi(N + 3, 0.0, 0.0, xh.data(), wh.data());
+  for (int k = 0; k <= N; ++k) {
+    double s = 0.0;
+    for (int q = 0; q < N + 3; ++q) {
+      const double P = jacobi_p(N - k, 2.0 * k + 3.0, 0.0, xh[q]);
+      s += wh[q] * std::pow(0.5 * (1.0 - xh[q]), 2 * k + 2) * P * P;
+    }
+    Ck[k] = s;
+  }
+  t.Ck = Ck;
+
+  std::vector<double> Lv(n1), dLv(n1);
+  std::vector<double> xq(Q), wq(Q), xqc(Q), wqc(Q);
+  gauss_jacobi(Q, 0.0, 0.0, xq.data(), wq.data());
+  gauss_jacobi(Q, 2.0, 0.0, xqc.data(), wqc.data());
+  for (int k = 0; k <= N; ++k) {
+    std::vector<double> xk(k + 1), wk(k + 1);
+    gauss_jacobi(k + 1, 0.0, 0.0, xk.data(), wk.data());
+    for (int i = 0; i <= k; ++i) t.geo[G.XL + tri_num(k) + i] = xk[i];
+    for (int p = 0; p < P3; ++p) {
+      lagrange(xk.data(), k + 1, xe[p], Lv.data(), dLv.data());
+      for (int i = 0; i <= k; ++i) {
+        t.tab[L.LX + (tri_num(k) + i) * P3 + p] = Lv[i];
+        if (p < n1) t.tab[L.DL + (tri_num(k) + i) * n1 + p] = dLv[i];
+      }
+    }
+    for (int p = 0; p < Q; ++p) {
+      lagrange(xk.data(), k + 1, xq[p], Lv.data(), dLv.data());
+      for (int i = 0; i <= k; ++i) t.geo[G.LQ + (tri_num(k) + i) * Q + p] = Lv[i];
+    }
+    for (int r = 0; r < n1; ++r) {
+      cfun(N, k, xc[r], &t.tab[L.GC + k * n1 + r], &t.tab[L.DGC + k * n1 + r], &t.tab[L.HC + k * n1 + r]);
+      cfun(N, k, xf[r], &t.tab[L.GF + k * n1 + r], nullptr, nullptr);
+    }
+    cfun(N, k, -1.0, &t.tab[L.GB + k], nullptr, nullptr);
+    for (int r = 0; r < Q; ++r) cfun(N, k, xqc[r], &t.geo[G.GQ + k * Q + r], nullptr, nullptr);
+    for (int j = 0; j <= k; ++j)
+      for (int i = 0; i <= k; ++i)
+        t.geo[G.IMR + lvl_off(k) + j * (k + 1) + i] = 1.0 / (wk[i] * wk[j] * Ck[k]);
+  }
+  for (int r = 0; r < n1; ++r) t.tab[L.WC + r] = 0.25 * wc[r];
+  for (int q = 0; q < n1; ++q)
+    for (int p = 0; p < n1; ++p) {
+      t.tab[L.WB + p + n1 * q] = wg[p] * wg[q];
+      t.tab[L.WFT + p + n1 * q] = wg[p] * 0.5 * wf[q];
+    }
+  for (int p = 0; p < n1; ++p) {
+    t.geo[G.XG + p] = xg[p];
+    t.geo[G.WG + p] = wg[p];
+    t.geo[G.XC + p] = xc[p];
+    t.geo[G.WC4 + p] = 0.25 * wc[p];
+    t.geo[G.XF + p] = xf[p];
+    t.geo[G.WF2 + p] = 0.5 * wf[p];
+  }
+  for (int p = 0; p < Q; ++p) {
+    t.geo[G.XQ + p] = xq[p];
+    t.geo[G.WQ + p] = wq[p];
+    t.geo[G.XQC + p] = xqc[p];
+    t.geo[G.WQC + p] = 0.25 * wqc[p];
+  }
+  (void)nrow;
+  (void)Np;
+  return 0;
+}
+
+// ------------------------------------------------------------------ geometry
+// Vertex map in collapsed coordinates: x(a,b,c) = (1-c)/2 B(a,b) + (1+c)/2 v5,
+// B the bilinear map of the base quadrilateral v1..v4 (the Bedrosian map of
+// Sec. 2 rewritten in (a,b,c)).
+static inline void bilinear(const double* v, double a, double b, double* B, double* Ba, double* Bb) {
+  const double w1 = 0.25 * (1 - a) * (1 - b), w2 = 0.25 * (1 + a) * (1 - b);
+  const double w3 = 0.25 * (1 + a) * (1 + b), w4 = 0.25 * (1 - a) * (1 + b);
+  for (int m = 0; m < 3; ++m) {
+    const double v1 = v[0 * 3 + m], v2 = v[1 * 3 + m], v3 = v[2 * 3 + m], v4 = v[3 * 3 + m];
+    if (B) B[m] = w1 * v1 + w2 * v2 + w3 * v3 + w4 * v4;
+    if (Ba) Ba[m] = 0.25 * ((1 - b) * (v2 - v1) + (1 + b) * (v3 - v4));
+    if (Bb) Bb[m] = 0.25 * ((1 - a) * (v4 - v1) + (1 + a) * (v3 - v2));
+  }
+}
+
+double jacobian_ab(const double* v, double a, double b) {
+  double B[3], Ba[3], Bb[3], D[3];
+  bilinear(v, a, b, B, Ba, Bb);
+  for (int m = 0; m < 3; ++m) D[m] = 0.5 * (v[12 + m] - B[m]);
+  // det[Ba, Bb, D] = Ba . (Bb x D)
+  const double cx = Bb[1] * D[2] - Bb[2] * D[1];
+  const double cy = Bb[2] * D[0] - Bb[0] * D[2];
+  const double cz = Bb[0] * D[1] - Bb[1] * D[0];
+  return Ba[0] * cx + Ba[1] * cy + Ba[2] * cz;
+}
+
+static inline void map_point(const double* v, double a, double b, double c, double* X) {
+  double B[3];
+  bilinear(v, a, b, B, nullptr, nullptr);
+  for (int m = 0; m < 3; ++m) X[m] = 0.5 * (1 - c) * B[m] + 0.5 * (1 + c) * v[12 + m];
+}
+
+static inline double norm3(const double* a) { return std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]); }
+static inline void cross3(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// |K| = int J = (8/3) J(0,0) (J bilinear in a,b; int ((1-c)/2)^2 dc = 2/3).
+// |dK| = base area by the (N+1)^2 Gauss-Legendre rule + the four triangle areas.
+double area_over_volume(const double* v, const double* xg, const double* wg, int n1) {
+  const double vol = (8.0 / 3.0) * jacobian_ab(v, 0.0, 0.0);
+  double area = 0.0;
+  for (int q = 0; q < n1; ++q)
+    for (int p = 0; p < n1; ++p) {
+      double Ba[3], Bb[3], c[3];
+      bilinear(v, xg[p], xg[q], nullptr, Ba, Bb);
+      cross3(Ba, Bb, c);
+      area += wg[p] * wg[q] * norm3(c);
+    }
+  static const int tri[4][3] = {{0, 1, 4}, {1, 2, 4}, {3, 2, 4}, {0, 3, 4}};
+  for (int f = 0; f < 4; ++f) {
+    double e1[3], e2[3], c[3];
+    for (int m = 0; m < 3; ++m) {
+      e1[m] = v[tri[f][1] * 3 + m] - v[tri[f][0] * 3 + m];
+      e2[m] = v[tri[f][2] * 3 + m] - v[tri[f][0] * 3 + m];
+    }
+    cross3(e1, e2, c);
+    area += 0.5 * norm3(c);
+  }
+  return area / vol;
+}
+
+// ----------------------------------------------------------- connectivity
+// Local vertex lists of the five faces (0-based v1..v5): base, b=-1, a=+1, b=+1, a=-1.
+static const int kFaceVerts[5][4] = {{0, 1, 2, 3}, {0, 1, 4, -1}, {1, 2, 4, -1}, {3, 2, 4, -1}, {0, 3, 4, -1}};
+
+// Cube coordinates of face point idx of face f.
+static inline void face_abc(int f, int idx, int n1, const double* xg, const double* xf, double* a, double* b,
+                            double* c) {
+  const int e = idx % n1, m = idx / n1;
+  switch (f) {
+    case 0: *a = xg[e]; *b = xg[m]; *c = -1.0; break;
+    case 1: *a = xg[e]; *b = -1.0; *c = xf[m]; break;
+    case 2: *a = 1.0; *b = xg[e]; *c = xf[m]; break;
+    case 3: *a = xg[e]; *b = 1.0; *c = xf[m]; break;
+    default: *a = -1.0; *b = xg[e]; *c = xf[m]; break;
+  }
+}
+
+// The symmetries of a face's point grid: the dihedral group of the square for
+// the base, edge reversal for a triangle (the apex stays the collapse point).
+static inline int permute(int code, int idx, int n1) {
+  const int N = n1 - 1;
+  const int p = idx % n1, q = idx / n1;
+  int pp = p, qq = q;
+  switch (code) {
+    case 0: pp = p; qq = q; break;
+    case 1: pp = N - p; qq = q; break;
+    case 2: pp = p; qq = N - q; break;
+    case 3: pp = N - p; qq = N - q; break;
+    case 4: pp = q; qq = p; break;
+    case 5: pp = N - q; qq = p; break;
+    case 6: pp = q; qq = N - p; break;
+    default: pp = N - q; qq = N - p; break;
+  }
+  return pp + n1 * qq;
+}
+
+struct FaceKey {
+  int64_t v[4];
+  int64_t elem;
+  int face;
+  bool operator<(const FaceKey& o) const {
+    for (int i = 0; i < 4; ++i)
+      if (v[i] != o.v[i]) return v[i] < o.v[i];
+    return elem != o.elem ? elem < o.elem : face < o.face;
+  }
+  bool same(const FaceKey& o) const { return v[0] == o.v[0] && v[1] == o.v[1] && v[2] == o.v[2] && v[3] == o.v[3]; }
+};
+
+int build_connectivity(const double* V, int64_t Nv, const int32_t* EToV, int64_t K, int N,
+                       std::vector<int64_t>& mapP, int64_t* nbnd, std::string& err) {
+  const int n1 = N + 1, n2 = n1 * n1, Nfc = 5 * n2;
+  std::vector<double> xg(n1), wg(n1), xf(n1), wf(n1);
+  gauss_jacobi(n1, 0.0, 0.0, xg.data(), wg.data());
+  gauss_jacobi(n1, 1.0, 0.0, xf.data(), wf.data());
+  for (int64_t e = 0; e < K; ++e)
+    for (int i = 0; i < 5; ++i)
+      if (EToV[e * 5 + i] < 0 || EToV[e * 5 + i] >= Nv) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "EToV[%lld][%d] = %d is outside [0, %lld)", (long long)e, i,
+                      EToV[e * 5 + i], (long long)Nv);
+        err = buf;
+        return -2;
+      }
+  std::vector<FaceKey> keys((size_t)K * 5);
+  for (int64_t e = 0; e < K; ++e)
+    for (int f = 0; f < 5; ++f) {
+      FaceKey& k = keys[(size_t)e * 5 + f];
+      const int nv = f == 0 ? 4 : 3;
+      for (int i = 0; i < 4; ++i) k.v[i] = i < nv ? (int64_t)EToV[e * 5 + kFaceVerts[f][i]] : INT64_MAX;
+      std::sort(k.v, k.v + 4);
+      k.elem = e;
+      k.face = f;
+    }
+  std::sort(keys.begin(), keys.end());
+  mapP.resize((size_t)K * Nfc);
+  for (int64_t g = 0; g < K * Nfc; ++g) mapP[(size_t)g] = g;
+  int64_t boundary = 0;
+  std::vector<double> X1((size_t)n2 * 3), X2((size_t)n2 * 3);
+  double ev1[15], ev2[15];
+  size_t i = 0;
+  while (i < keys.size()) {
+    size_t j = i + 1;
+    while (j < keys.size() && keys[j].same(keys[i])) ++j;
+    if (j - i > 2) {
+      err = "a face is shared by more than two elements";
+      return -2;
+    }
+    if (j - i == 1) {
+      ++boundary;
+      i = j;
+      continue;
+    }
+    const FaceKey &A = keys[i], &B = keys[i + 1];
+    for (int m = 0; m < 15; ++m) {
+      ev1[m] = V[(int64_t)EToV[A.elem * 5 + m / 3] * 3 + m % 3];
+      ev2[m] = V[(int64_t)EToV[B.elem * 5 + m / 3] * 3 + m % 3];
+    }
+    double scale = 0.0;
+    for (int idx = 0; idx < n2; ++idx) {
+      double a, b, c;
+      face_abc(A.face, idx, n1, xg.data(), xf.data(), &a, &b, &c);
+      map_point(ev1, a, b, c, &X1[(size_t)idx * 3]);
+      face_abc(B.face, idx, n1, xg.data(), xf.data(), &a, &b, &c);
+      map_point(ev2, a, b, c, &X2[(size_t)idx * 3]);
+    }
+    for (int m = 0; m < 3; ++m) {
+      double lo = X1[m], hi = X1[m];
+      for (int idx = 1; idx < n2; ++idx) {
+        lo = std::min(lo, X1[(size_t)idx * 3 + m]);
+        hi = std::max(hi, X1[(size_t)idx * 3 + m]);
+      }
+      scale = std::max(scale, hi - lo);
+    }
+    const double tol = 1e-9 * scale;
+    const int ncodes = A.face == 0 ? 8 : 2;
+    int found = -1;
+    for (int code = 0; code < ncodes && found < 0; ++code) {
+      bool ok = true;
+      for (int idx = 0; idx < n2 && ok; ++idx) {
+        const int jdx = permute(code, idx, n1);
+        for (int m = 0; m < 3; ++m)
+          if (std::fabs(X1[(size_t)idx * 3 + m] - X2[(size_t)jdx * 3 + m]) > tol) ok = false;
+      }
+      if (ok) found = code;
+    }
+    if (found < 0) {
+      char buf[200];
+      std::snprintf(buf, sizeof buf,
+                    "face %d of element %lld and face %d of element %lld share vertices but not cubature "
+                    "points (non-conforming collapse)",
+                    A.face, (long long)A.elem, B.face, (long long)B.elem);
+      err = buf;
+      return -2;
+    }
+    for (int idx = 0; idx < n2; ++idx) {
+      const int jdx = permute(found, idx, n1);
+      const int64_t ga = A.elem * Nfc + (int64_t)A.face * n2 + idx;
+      const int64_t gb = B.elem * Nfc + (int64_t)B.face * n2 + jdx;
+      mapP[(size_t)ga] = gb;
+      mapP[(size_t)gb] = ga;
+    }
+    i = j;
+  }
+  if (nbnd) *nbnd = boundary;
+  return 0;
+}
+
+}  // namespace pyrdg

@@ -1,0 +1,675 @@
+// CUDA kernels of one LSRK stage of the pyramid DG acoustic-wave method
+// (Sec. 4.2 Alg. 1-3 with the semi-nodal basis of Lemma 3), templated on the
+// degree N and the scalar type T (double or float).
+//
+// Sum factorisation. phi_ijk(a,b,c) = l_i^k(a) l_j^k(b) G_k(c) and the volume
+// rule is a tensor grid (a_p, b_q, c_r), so every interpolation and every
+// projection factors into three one-dimensional passes (a, then b, then c, or
+// the reverse). Face points reuse the same passes: the base face is c = -1 on
+// the (a_p, b_q) grid, the triangle faces sit at a = +-1 or b = +-1, which are
+// the two extra entries (-1, +1) appended to the a and b point sets.
+//
+// One CTA processes one element; all intermediates live in shared memory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "layout.h"
+
+namespace pyrdg {
+
+template <int N>
+struct KCfg {
+  using d = Dims<N>;
+  static constexpr int NT = d::Nc <= 128 ? 128 : (d::Nc <= 256 ? 256 : 512);
+  static constexpr int NT_ERR = 256;
+};
+
+__device__ __forceinline__ void decode_mode(int n, int& k, int& j, int& i) {
+  k = 0;
+  while (lvl_off(k + 1) <= n) ++k;
+  const int rem = n - lvl_off(k);
+  j = rem / (k + 1);
+  i = rem - j * (k + 1);
+}
+
+__device__ __forceinline__ void decode_row(int row, int& k, int& j) {
+  k = 0;
+  while (tri_num(k + 1) <= row) ++k;
+  j = row - tri_num(k);
+}
+
+template <typename T>
+__device__ __forceinline__ size_t align_up(size_t x) {
+  return (x + 15) & ~size_t(15);
+}
+
+// Bilinear base map B(a,b) of v1..v4 and its a, b derivatives (double).
+__device__ __forceinline__ void d_bilinear(const double* v, double a, double b, double* B, double* Ba, double* Bb) {
+  const double w1 = 0.25 * (1 - a) * (1 - b), w2 = 0.25 * (1 + a) * (1 - b);
+  const double w3 = 0.25 * (1 + a) * (1 + b), w4 = 0.25 * (1 - a) * (1 + b);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const double v1 = v[m], v2 = v[3 + m], v3 = v[6 + m], v4 = v[9 + m];
+    B[m] = w1 * v1 + w2 * v2 + w3 * v3 + w4 * v4;
+    Ba[m] = 0.25 * ((1 - b) * (v2 - v1) + (1 + b) * (v3 - v4));
+    Bb[m] = 0.25 * ((1 - a) * (v4 - v1) + (1 + a) * (v3 - v2));
+  }
+}
+
+__device__ __forceinline__ void d_cross(const double* a, const double* b, double* c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// J(a,b) = det[B_a, B_b, D], D = (v5 - B)/2 (Lemma 1: bilinear in a, b).
+__device__ __forceinline__ double d_jacobian(const double* v, double a, double b) {
+  double B[3], Ba[3], Bb[3], D[3], g1[3];
+  d_bilinear(v, a, b, B, Ba, Bb);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) D[m] = 0.5 * (v[12 + m] - B[m]);
+  d_cross(Bb, D, g1);
+  return Ba[0] * g1[0] + Ba[1] * g1[1] + Ba[2] * g1[2];
+}
+
+// Exact standing waves (wall on [0,1]^3, free surface on [-1,1]^3).
+__device__ __forceinline__ void d_exact(int bc, double x, double y, double z, double t, double* out) {
+  const double k = bc == 0 ? 3.14159265358979323846 : 1.57079632679489661923;
+  const double s3 = 1.7320508075688772935;
+  const double om = s3 * k;
+  double sx, cx, sy, cy, sz, cz, st, ct;
+  sincos(k * x, &sx, &cx);
+  sincos(k * y, &sy, &cy);
+  sincos(k * z, &sz, &cz);
+  sincos(om * t, &st, &ct);
+  out[0] = cx * cy * cz * ct;
+  out[1] = sx * cy * cz * st / s3;
+  out[2] = cx * sy * cz * st / s3;
+  out[3] = cx * cy * sz * st / s3;
+}
+
+// ============================================================ geometry (a1)
+// Per element, in double: at the (a_p, b_q) grid the nine factors
+// w_p w_q (g1, g2, g3), g1 = B_b x D, g2 = D x B_a, g3 = B_a x B_b, so that
+// J grad(u) = u_r g1 + u_s g2 + u_c g3 with u_r = 2/(1-c) u_a, u_s = 2/(1-c) u_b
+// (all c-independent); base-face unit normal and surface Jacobian from
+// n sJ = -g3; triangle faces: constant n sJ from the face's edge and apex;
+// mass diagonal inverse 1/(J(a_i^k, b_j^k) w_i^k w_j^k C_k) (Lemma 3).
+template <int N, typename T>
+__global__ void geom_kernel(int64_t K, const double* __restrict__ ev, const double* __restrict__ gtab,
+                            T* __restrict__ geo, T* __restrict__ gface, T* __restrict__ invM) {
+  using d = Dims<N>;
+  constexpr GeoLayout G(N);
+  const int64_t e = blockIdx.x;
+  __shared__ double v[15];
+  if (threadIdx.x < 15) v[threadIdx.x] = ev[e * 15 + threadIdx.x];
+  __syncthreads();
+  for (int pq = threadIdx.x; pq < d::n2; pq += blockDim.x) {
+    const int p = pq % d::n1, q = pq / d::n1;
+    const double a = gtab[G.XG + p], b = gtab[G.XG + q];
+    double B[3], Ba[3], Bb[3], D[3], g1[3], g2[3], g3[3];
+    d_bilinear(v, a, b, B, Ba, Bb);
+    for (int m = 0; m < 3; ++m) D[m] = 0.5 * (v[12 + m] - B[m]);
+    d_cross(Bb, D, g1);
+    d_cross(D, Ba, g2);
+    d_cross(Ba, Bb, g3);
+    const double w = gtab[G.WG + p] * gtab[G.WG + q];
+    T* out = geo + (e * d::n2 + pq) * d::NGEO;
+    for (int m = 0; m < 3; ++m) {
+      out[m] = (T)(w * g1[m]);
+      out[3 + m] = (T)(w * g2[m]);
+      out[6 + m] = (T)(w * g3[m]);
+    }
+    const double sJ = sqrt(g3[0] * g3[0] + g3[1] * g3[1] + g3[2] * g3[2]);
+    T* gf = gface + e * d::NGF + 16 + 4 * pq;
+    for (int m = 0; m < 3; ++m) gf[m] = (T)(-g3[m] / sJ);
+    gf[3] = (T)sJ;
+  }
+  if (threadIdx.x < 4) {
+    // faces b=-1, a=+1, b=+1, a=-1: outward n sJ = (x1 - x0) x (x2 - x0) / 4
+    const int f = threadIdx.x;
+    // b=-1: (v2-v1)x(v5-v1); a=+1: (v3-v2)x(v5-v2); b=+1: (v3-v5)x(v4-v5); a=-1: (v5-v1)x(v4-v1)
+    const int i0[4] = {0, 1, 4, 0}, i1[4] = {1, 2, 2, 4}, i2[4] = {4, 4, 3, 3};
+    double e1[3], e2[3], ns[3];
+    for (int m = 0; m < 3; ++m) {
+      e1[m] = v[i1[f] * 3 + m] - v[i0[f] * 3 + m];
+      e2[m] = v[i2[f] * 3 + m] - v[i0[f] * 3 + m];
+    }
+    d_cross(e1, e2, ns);
+    const double sJ = 0.25 * sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
+    T* gf = gface + e * d::NGF + 4 * f;
+    for (int m = 0; m < 3; ++m) gf[m] = (T)(0.25 * ns[m] / sJ);
+    gf[3] = (T)sJ;
+  }
+  for (int n = threadIdx.x; n < d::Np; n += blockDim.x) {
+    int k, j, i;
+    decode_mode(n, k, j, i);
+    const double J = d_jacobian(v, gtab[G.XL + tri_num(k) + i], gtab[G.XL + tri_num(k) + j]);
+    invM[e * d::Np + n] = (T)(gtab[G.IMR + n] / J);
+  }
+}
+
+// ============================================================ trace (a2)
+// u^f = V^f u at all 5(N+1)^2 face points for the four fields; the output
+// tr[(e*Nfc + g)*4 + field] feeds the neighbours' flux in the next kernel.
+template <int N, typename T>
+struct TraceSmem {
+  using d = Dims<N>;
+  static constexpr int nB = d::n2 + 4 * d::n1;  // base grid + 4 face rows per level
+  static constexpr size_t tab = 0;
+  static constexpr size_t u = tab + TabLayout(N).size;
+  static constexpr size_t A = u + 4 * d::Np;
+  static constexpr size_t B = A + 4 * d::nrow * d::P3;
+  static constexpr size_t total = B + 4 * d::n1 * nB;
+  static constexpr size_t bytes = total * sizeof(T);
+};
+
+template <int N, typename T>
+__global__ void __launch_bounds__(KCfg<N>::NT) trace_kernel(int64_t K, const T* __restrict__ q,
+                                                            const T* __restrict__ tab, T* __restrict__ tr) {
+  using d = Dims<N>;
+  using S = TraceSmem<N, T>;
+  constexpr TabLayout L(N);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* s_tab = sm + S::tab;
+  T* s_u = sm + S::u;
+  T* s_A = sm + S::A;
+  T* s_B = sm + S::B;
+  const int64_t e = blockIdx.x;
+  const int tid = threadIdx.x;
+  for (int x = tid; x < L.size; x += blockDim.x) s_tab[x] = tab[x];
+  for (int x = tid; x < 4 * d::Np; x += blockDim.x) s_u[x] = q[e * 4 * d::Np + x];
+  __syncthreads();
+  // a pass: A[f][row(k,j)][p'] = sum_i l_i^k(x_p') u[f][k][j][i], p' over GL points and -1, +1
+  for (int x = tid; x < 4 * d::nrow * d::P3; x += blockDim.x) {
+    const int pp = x % d::P3;
+    const int t = x / d::P3;
+    const int row = t % d::nrow, f = t / d::nrow;
+    int k, j;
+    decode_row(row, k, j);
+    const T* uc = s_u + f * d::Np + lvl_off(k) + j * (k + 1);
+    const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + pp;
+    T acc = 0;
+    for (int i = 0; i <= k; ++i) acc += uc[i] * lx[i * d::P3];
+    s_A[x] = acc;
+  }
+  __syncthreads();
+  // b pass per level k: base grid (p,q) and the four triangle-face rows
+  for (int x = tid; x < 4 * d::n1 * S::nB; x += blockDim.x) {
+    const int s = x % S::nB;
+    const int t = x / S::nB;
+    const int k = t % d::n1, f = t / d::n1;
+    int pa, qb;  // A column (a point) and l^k_j evaluation column (b point)
+    if (s < d::n2) {
+      pa = s % d::n1;
+      qb = s / d::n1;
+    } else {
+      const int slot = (s - d::n2) / d::n1, ee = (s - d::n2) % d::n1;
+      // slot 0: b=-1 (face 1), 1: b=+1 (face 3), 2: a=-1 (face 4), 3: a=+1 (face 2)
+      if (slot < 2) {
+        pa = ee;
+        qb = d::n1 + slot;
+      } else {
+        pa = d::n1 + (slot - 2);
+        qb = ee;
+      }
+    }
+    const T* Ar = s_A + (f * d::nrow + tri_num(k)) * d::P3 + pa;
+    const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + qb;
+    T acc = 0;
+    for (int j = 0; j <= k; ++j) acc += Ar[j * d::P3] * lx[j * d::P3];
+    s_B[x] = acc;
+  }
+  __syncthreads();
+  // c pass: sum over levels with G_k(-1) (base) or G_k(c_m) (triangles)
+  for (int g = tid; g < d::Nfc; g += blockDim.x) {
+    const int face = g / d::n2, idx = g % d::n2;
+    T out[4];
+    if (face == 0) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        T acc = 0;
+        for (int k = 0; k <= N; ++k) acc += s_tab[L.GB + k] * s_B[(f * d::n1 + k) * S::nB + idx];
+        out[f] = acc;
+      }
+    } else {
+      const int ee = idx % d::n1, m = idx / d::n1;
+      const int slot = face == 1 ? 0 : face == 3 ? 1 : face == 4 ? 2 : 3;
+      const int s = d::n2 + slot * d::n1 + ee;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        T acc = 0;
+        for (int k = 0; k <= N; ++k) acc += s_tab[L.GF + k * d::n1 + m] * s_B[(f * d::n1 + k) * S::nB + s];
+        out[f] = acc;
+      }
+    }
+    T* dst = tr + (e * d::Nfc + g) * 4;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) dst[f] = out[f];
+  }
+}
+
+// ===================================================== rhs / update (a3-a7)
+template <int N, typename T>
+struct RhsSmem {
+  using d = Dims<N>;
+  static constexpr int nY = d::P3 * d::P3;
+  static constexpr size_t tab = 0;
+  static constexpr size_t u = tab + TabLayout(N).size;
+  static constexpr size_t geo = u + 4 * d::Np;
+  static constexpr size_t gf = geo + d::NGEO * d::n2;
+  static constexpr size_t Fs = gf + d::NGF;
+  static constexpr size_t A = Fs + 4 * d::Nfc;
+  static constexpr size_t dA = A + 4 * d::nrow * d::n1;
+  static constexpr size_t U = dA + 4 * d::nrow * d::n1;
+  static constexpr size_t Ua = U + 4 * d::n1 * d::n2;
+  static constexpr size_t Ub = Ua + 4 * d::n1 * d::n2;
+  // after the c pass U/Ua/Ub are dead: Y and Z reuse their space
+  static constexpr size_t Y = U;
+  static constexpr size_t Z = Y + 4 * d::n1 * nY;
+  static constexpr size_t R1 = 3 * 4 * d::n1 * d::n2;
+  static constexpr size_t R2 = 4 * d::n1 * nY + 4 * d::nrow * d::P3;
+  static constexpr size_t Fv = U + (R1 > R2 ? R1 : R2);
+  static constexpr size_t total = Fv + 4 * d::Nc;
+  static constexpr size_t bytes = total * sizeof(T);
+};
+
+// Surface flux of Sec. 4.3 at one face point, scaled by weight * sJ:
+// F_p = 1/2 (n.[[u]] - tau [[p]]), F_u = 1/2 n ([[p]] - tau n.[[u]]).
+template <typename T>
+__device__ __forceinline__ void face_flux(const T* um, const T* up_in, bool boundary, int bc, T tau, const T* n,
+                                          T ws, T* F) {
+  T up[4];
+  if (!boundary) {
+    up[0] = up_in[0];
+    up[1] = up_in[1];
+    up[2] = up_in[2];
+    up[3] = up_in[3];
+  } else if (bc == 0) {  // wall: mirror the normal velocity
+    const T un = n[0] * um[1] + n[1] * um[2] + n[2] * um[3];
+    up[0] = um[0];
+    up[1] = um[1] - 2 * un * n[0];
+    up[2] = um[2] - 2 * un * n[1];
+    up[3] = um[3] - 2 * un * n[2];
+  } else {  // free surface p = 0
+    up[0] = -um[0];
+    up[1] = um[1];
+    up[2] = um[2];
+    up[3] = um[3];
+  }
+  const T dp = up[0] - um[0];
+  const T nd = n[0] * (up[1] - um[1]) + n[1] * (up[2] - um[2]) + n[2] * (up[3] - um[3]);
+  const T hp = T(0.5) * ws * (nd - tau * dp);
+  const T hu = T(0.5) * ws * (dp - tau * nd);
+  F[0] = hp;
+  F[1] = hu * n[0];
+  F[2] = hu * n[1];
+  F[3] = hu * n[2];
+}
+
+// Transposed passes shared by the rhs and projection kernels: from point
+// data Fv[f][r*n2 + pq] (already weighted) and face data Fs[f][g] (already
+// weighted; may be null) to the projections sum_q phi_n(x_q) F_q into out.
+template <int N, typename T>
+__device__ __forceinline__ void project_passes(const T* s_tab, const T* Fv, const T* Fs, T* Y, T* Z, int tid,
+                                               int nthr) {
+  using d = Dims<N>;
+  constexpr TabLayout L(N);
+  constexpr int nY = d::P3 * d::P3;
+  constexpr int nS = d::n2 + 4 * d::n1;
+  // c^T pass: Y[f][k][p'][q']
+  for (int x = tid; x < 4 * d::n1 * nS; x += nthr) {
+    const int s = x % nS;
+    const int t = x / nS;
+    const int k = t % d::n1, f = t / d::n1;
+    T* Yk = Y + (f * d::n1 + k) * nY;
+    if (s < d::n2) {
+      const int p = s % d::n1, q = s / d::n1;
+      const T* fv = Fv + f * d::Nc + s;
+      const T* gc = s_tab + L.GC + k * d::n1;
+      T acc = 0;
+      for (int r = 0; r < d::n1; ++r) acc += gc[r] * fv[r * d::n2];
+      if (Fs) acc += s_tab[L.GB + k] * Fs[f * d::Nfc + s];
+      Yk[p * d::P3 + q] = acc;
+    } else if (Fs) {
+      const int slot = (s - d::n2) / d::n1, ee = (s - d::n2) % d::n1;
+      const int face = slot == 0 ? 1 : slot == 1 ? 3 : slot == 2 ? 4 : 2;
+      const T* fs = Fs + f * d::Nfc + face * d::n2 + ee;
+      const T* gfk = s_tab + L.GF + k * d::n1;
+      T acc = 0;
+      for (int m = 0; m < d::n1; ++m) acc += gfk[m] * fs[m * d::n1];
+      if (slot < 2)
+        Yk[ee * d::P3 + d::n1 + slot] = acc;  // b = -1, +1 columns
+      else
+        Yk[(d::n1 + slot - 2) * d::P3 + ee] = acc;  // a = -1, +1 rows
+    }
+  }
+  __syncthreads();
+  // b^T pass: Z[f][row(k,j)][p'] = sum_q' l_j^k(x_q') Y[f][k][p'][q']
+  const int nq_main = Fs ? d::P3 : d::n1;
+  const int np_out = Fs ? d::P3 : d::n1;
+  for (int x = tid; x < 4 * d::nrow * np_out; x += nthr) {
+    const int pp = x % np_out;
+    const int t = x / np_out;
+    const int row = t % d::nrow, f = t / d::nrow;
+    int k, j;
+    decode_row(row, k, j);
+    const T* Yr = Y + ((f * d::n1 + k) * d::P3 + pp) * d::P3;
+    const T* lx = s_tab + L.LX + (tri_num(k) + j) * d::P3;
+    const int nq = pp < d::n1 ? nq_main : d::n1;
+    T acc = 0;
+    for (int q = 0; q < nq; ++q) acc += lx[q] * Yr[q];
+    Z[(f * d::nrow + row) * d::P3 + pp] = acc;
+  }
+  __syncthreads();
+}
+
+template <int N, typename T, bool UPDATE>
+__global__ void __launch_bounds__(KCfg<N>::NT)
+    rhs_kernel(int64_t K, const T* qin, T* qout, T* __restrict__ res,  // qin == qout when updating in place
+               const T* __restrict__ tr, const int32_t* __restrict__ mapP, const T* __restrict__ geo,
+               const T* __restrict__ gface, const T* __restrict__ invM, const T* __restrict__ tab, int bc, T tau,
+               T rka, T rkb, T dt) {
+  using d = Dims<N>;
+  using S = RhsSmem<N, T>;
+  constexpr TabLayout L(N);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* s_tab = sm + S::tab;
+  T* s_u = sm + S::u;
+  T* s_geo = sm + S::geo;
+  T* s_gf = sm + S::gf;
+  T* s_Fs = sm + S::Fs;
+  T* s_A = sm + S::A;
+  T* s_dA = sm + S::dA;
+  T* s_U = sm + S::U;
+  T* s_Ua = sm + S::Ua;
+  T* s_Ub = sm + S::Ub;
+  T* s_Fv = sm + S::Fv;
+  T* s_Y = sm + S::Y;
+  T* s_Z = sm + S::Z;
+  const int64_t e = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int nthr = blockDim.x;
+
+  for (int x = tid; x < L.size; x += nthr) s_tab[x] = tab[x];
+  for (int x = tid; x < 4 * d::Np; x += nthr) s_u[x] = qin[e * 4 * d::Np + x];
+  for (int x = tid; x < d::NGEO * d::n2; x += nthr) s_geo[x] = geo[e * d::NGEO * d::n2 + x];
+  for (int x = tid; x < d::NGF; x += nthr) s_gf[x] = gface[e * d::NGF + x];
+  __syncthreads();
+
+  // surface flux at every face point (a4), weighted by w sJ
+  for (int g = tid; g < d::Nfc; g += nthr) {
+    const int face = g / d::n2, idx = g % d::n2;
+    const int64_t gl = e * d::Nfc + g;
+    const int64_t gn = mapP[gl];
+    T um[4], up[4], F[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      um[f] = tr[gl * 4 + f];
+      up[f] = tr[gn * 4 + f];
+    }
+    const T* nv = face == 0 ? s_gf + 16 + 4 * idx : s_gf + 4 * (face - 1);
+    const T w = face == 0 ? s_tab[L.WB + idx] : s_tab[L.WFT + idx];
+    face_flux<T>(um, up, gn == gl, bc, tau, nv, w * nv[3], F);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) s_Fs[f * d::Nfc + g] = F[f];
+  }
+  // a pass: A = l(a_p) u, dA = l'(a_p) u
+  for (int x = tid; x < 4 * d::nrow * d::n1; x += nthr) {
+    const int p = x % d::n1;
+    const int t = x / d::n1;
+    const int row = t % d::nrow, f = t / d::nrow;
+    int k, j;
+    decode_row(row, k, j);
+    const T* uc = s_u + f * d::Np + lvl_off(k) + j * (k + 1);
+    const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + p;
+    const T* dl = s_tab + L.DL + tri_num(k) * d::n1 + p;
+    T a = 0, da = 0;
+    for (int i = 0; i <= k; ++i) {
+      a += uc[i] * lx[i * d::P3];
+      da += uc[i] * dl[i * d::n1];
+    }
+    s_A[x] = a;
+    s_dA[x] = da;
+  }
+  __syncthreads();
+  // b pass: U_k, (d_a U)_k, (d_b U)_k on the (a_p, b_q) grid
+  for (int x = tid; x < 4 * d::n1 * d::n2; x += nthr) {
+    const int pq = x % d::n2;
+    const int t = x / d::n2;
+    const int k = t % d::n1, f = t / d::n1;
+    const int p = pq % d::n1, q = pq / d::n1;
+    const T* Ar = s_A + (f * d::nrow + tri_num(k)) * d::n1 + p;
+    const T* dAr = s_dA + (f * d::nrow + tri_num(k)) * d::n1 + p;
+    const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + q;
+    const T* dl = s_tab + L.DL + tri_num(k) * d::n1 + q;
+    T u = 0, ua = 0, ub = 0;
+    for (int j = 0; j <= k; ++j) {
+      const T av = Ar[j * d::n1], lv = lx[j * d::P3];
+      u += av * lv;
+      ub += av * dl[j * d::n1];
+      ua += dAr[j * d::n1] * lv;
+    }
+    s_U[x] = u;
+    s_Ua[x] = ua;
+    s_Ub[x] = ub;
+  }
+  __syncthreads();
+  // c pass + chain rule (Alg. 1): weighted J div(u) and J grad(p) at the volume points
+  for (int x = tid; x < d::Nc; x += nthr) {
+    const int pq = x % d::n2, r = x / d::n2;
+    const T* hc = s_tab + L.HC + r;
+    const T* dg = s_tab + L.DGC + r;
+    T d3[4][3];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const T* Uf = s_U + f * d::n1 * d::n2 + pq;
+      const T* Uaf = s_Ua + f * d::n1 * d::n2 + pq;
+      const T* Ubf = s_Ub + f * d::n1 * d::n2 + pq;
+      T ur = 0, us = 0, uc = 0;
+#pragma unroll
+      for (int k = 0; k <= N; ++k) {
+        ur += hc[k * d::n1] * Uaf[k * d::n2];
+        us += hc[k * d::n1] * Ubf[k * d::n2];
+        uc += dg[k * d::n1] * Uf[k * d::n2];
+      }
+      d3[f][0] = ur;
+      d3[f][1] = us;
+      d3[f][2] = uc;
+    }
+    const T* g = s_geo + pq * d::NGEO;  // w_p w_q (g1, g2, g3)
+    const T wc = s_tab[L.WC + r];
+    const T px = d3[0][0] * g[0] + d3[0][1] * g[3] + d3[0][2] * g[6];
+    const T py = d3[0][0] * g[1] + d3[0][1] * g[4] + d3[0][2] * g[7];
+    const T pz = d3[0][0] * g[2] + d3[0][1] * g[5] + d3[0][2] * g[8];
+    const T ux = d3[1][0] * g[0] + d3[1][1] * g[3] + d3[1][2] * g[6];
+    const T vy = d3[2][0] * g[1] + d3[2][1] * g[4] + d3[2][2] * g[7];
+    const T wz = d3[3][0] * g[2] + d3[3][1] * g[5] + d3[3][2] * g[8];
+    s_Fv[0 * d::Nc + x] = wc * (ux + vy + wz);
+    s_Fv[1 * d::Nc + x] = wc * px;
+    s_Fv[2 * d::Nc + x] = wc * py;
+    s_Fv[3 * d::Nc + x] = wc * pz;
+  }
+  __syncthreads();
+  // projections: volume (V^T) and lift ((V^f)^T) in the same transposed passes
+  project_passes<N, T>(s_tab, s_Fv, s_Fs, s_Y, s_Z, tid, nthr);
+  // a^T pass, M^{-1} (a6), LSRK stage (a7)
+  for (int x = tid; x < 4 * d::Np; x += nthr) {
+    const int f = x / d::Np, n = x % d::Np;
+    int k, j, i;
+    decode_mode(n, k, j, i);
+    const T* lx = s_tab + L.LX + (tri_num(k) + i) * d::P3;
+    const T* Zr = s_Z + (f * d::nrow + tri_num(k) + j) * d::P3;
+    T acc = 0;
+#pragma unroll
+    for (int pp = 0; pp < d::P3; ++pp) acc += lx[pp] * Zr[pp];
+    const T rhs = -invM[e * d::Np + n] * acc;
+    const int64_t gi = e * 4 * d::Np + x;
+    if (UPDATE) {
+      const T rnew = rka * res[gi] + dt * rhs;
+      res[gi] = rnew;
+      qout[gi] = s_u[x] + rkb * rnew;
+    } else {
+      qout[gi] = rhs;
+    }
+  }
+}
+
+// ============================================================ projection
+// L2 projection of the exact standing wave at time t (double arithmetic):
+// coefficient = M^{-1} sum_q w_q J_q phi_n(x_q) U_exact(x_q).
+template <int N>
+struct ProjSmem {
+  using d = Dims<N>;
+  static constexpr size_t tab = 0;
+  static constexpr size_t Fv = tab + TabLayout(N).size;
+  static constexpr size_t Y = Fv + 4 * d::Nc;
+  static constexpr size_t Z = Y + 4 * d::n1 * d::P3 * d::P3;
+  static constexpr size_t total = Z + 4 * d::nrow * d::P3;
+  static constexpr size_t bytes = total * sizeof(double);
+};
+
+template <int N, typename T>
+__global__ void __launch_bounds__(KCfg<N>::NT)
+    project_kernel(int64_t K, const double* __restrict__ ev, const double* __restrict__ gtab,
+                   const double* __restrict__ tabd, int bc, double t, T* __restrict__ qout) {
+  using d = Dims<N>;
+  using S = ProjSmem<N>;
+  constexpr TabLayout L(N);
+  constexpr GeoLayout G(N);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sm = reinterpret_cast<double*>(smem_raw);
+  double* s_tab = sm + S::tab;
+  double* s_Fv = sm + S::Fv;
+  double* s_Y = sm + S::Y;
+  double* s_Z = sm + S::Z;
+  __shared__ double v[15];
+  const int64_t e = blockIdx.x;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int x = tid; x < L.size; x += nthr) s_tab[x] = tabd[x];
+  if (tid < 15) v[tid] = ev[e * 15 + tid];
+  __syncthreads();
+  for (int x = tid; x < d::Nc; x += nthr) {
+    const int pq = x % d::n2, r = x / d::n2;
+    const int p = pq % d::n1, q = pq / d::n1;
+    const double a = gtab[G.XG + p], b = gtab[G.XG + q], c = gtab[G.XC + r];
+    double B[3], Ba[3], Bb[3], X[3], U[4];
+    d_bilinear(v, a, b, B, Ba, Bb);
+    for (int m = 0; m < 3; ++m) X[m] = 0.5 * (1 - c) * B[m] + 0.5 * (1 + c) * v[12 + m];
+    const double w = gtab[G.WG + p] * gtab[G.WG + q] * gtab[G.WC4 + r] * d_jacobian(v, a, b);
+    d_exact(bc, X[0], X[1], X[2], t, U);
+    for (int f = 0; f < 4; ++f) s_Fv[f * d::Nc + x] = w * U[f];
+  }
+  __syncthreads();
+  project_passes<N, double>(s_tab, s_Fv, nullptr, s_Y, s_Z, tid, nthr);
+  for (int x = tid; x < 4 * d::Np; x += nthr) {
+    const int f = x / d::Np, n = x % d::Np;
+    int k, j, i;
+    decode_mode(n, k, j, i);
+    const double* lx = s_tab + L.LX + (tri_num(k) + i) * d::P3;
+    const double* Zr = s_Z + (f * d::nrow + tri_num(k) + j) * d::P3;
+    double acc = 0;
+    for (int pp = 0; pp < d::n1; ++pp) acc += lx[pp] * Zr[pp];
+    const double J = d_jacobian(v, gtab[G.XL + tri_num(k) + i], gtab[G.XL + tri_num(k) + j]);
+    qout[e * 4 * d::Np + x] = (T)(acc * gtab[G.IMR + n] / J);
+  }
+}
+
+// ============================================================ error norm (a8)
+// sum over elements and (N+3)^3 points of w J |U_h - U_exact|^2 and w J |U_exact|^2,
+// in double; grid-stride over elements, one partial pair per block.
+template <int N>
+struct ErrSmem {
+  using d = Dims<N>;
+  static constexpr int Q = d::Q;
+  static constexpr size_t u = 0;
+  static constexpr size_t A = u + 4 * d::Np;
+  static constexpr size_t B = A + 4 * d::nrow * Q;
+  static constexpr size_t total = B + 4 * d::n1 * Q * Q;
+  static constexpr size_t bytes = total * sizeof(double);
+};
+
+template <int N, typename T>
+__global__ void __launch_bounds__(256)
+    error_kernel(int64_t K, const T* __restrict__ q, const double* __restrict__ ev, const double* __restrict__ gtab,
+                 int bc, double t, double* __restrict__ partial) {
+  using d = Dims<N>;
+  using S = ErrSmem<N>;
+  constexpr GeoLayout G(N);
+  constexpr int Q = d::Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sm = reinterpret_cast<double*>(smem_raw);
+  double* s_u = sm + S::u;
+  double* s_A = sm + S::A;
+  double* s_B = sm + S::B;
+  __shared__ double v[15];
+  __shared__ double red[2][256];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  double e2 = 0.0, n2 = 0.0;
+  for (int64_t e = blockIdx.x; e < K; e += gridDim.x) {
+    __syncthreads();
+    for (int x = tid; x < 4 * d::Np; x += nthr) s_u[x] = (double)q[e * 4 * d::Np + x];
+    if (tid < 15) v[tid] = ev[e * 15 + tid];
+    __syncthreads();
+    for (int x = tid; x < 4 * d::nrow * Q; x += nthr) {
+      const int p = x % Q;
+      const int tt = x / Q;
+      const int row = tt % d::nrow, f = tt / d::nrow;
+      int k, j;
+      decode_row(row, k, j);
+      const double* uc = s_u + f * d::Np + lvl_off(k) + j * (k + 1);
+      double acc = 0;
+      for (int i = 0; i <= k; ++i) acc += uc[i] * gtab[G.LQ + (tri_num(k) + i) * Q + p];
+      s_A[x] = acc;
+    }
+    __syncthreads();
+    for (int x = tid; x < 4 * d::n1 * Q * Q; x += nthr) {
+      const int pq = x % (Q * Q);
+      const int tt = x / (Q * Q);
+      const int k = tt % d::n1, f = tt / d::n1;
+      const int p = pq % Q, qq = pq / Q;
+      double acc = 0;
+      for (int j = 0; j <= k; ++j)
+        acc += s_A[(f * d::nrow + tri_num(k) + j) * Q + p] * gtab[G.LQ + (tri_num(k) + j) * Q + qq];
+      s_B[x] = acc;
+    }
+    __syncthreads();
+    for (int x = tid; x < Q * Q * Q; x += nthr) {
+      const int pq = x % (Q * Q), r = x / (Q * Q);
+      const int p = pq % Q, qq = pq / Q;
+      const double a = gtab[G.XQ + p], b = gtab[G.XQ + qq], c = gtab[G.XQC + r];
+      double B[3], Ba[3], Bb[3], X[3], Ue[4];
+      d_bilinear(v, a, b, B, Ba, Bb);
+      for (int m = 0; m < 3; ++m) X[m] = 0.5 * (1 - c) * B[m] + 0.5 * (1 + c) * v[12 + m];
+      const double w = gtab[G.WQ + p] * gtab[G.WQ + qq] * gtab[G.WQC + r] * d_jacobian(v, a, b);
+      d_exact(bc, X[0], X[1], X[2], t, Ue);
+      for (int f = 0; f < 4; ++f) {
+        double uh = 0;
+        for (int k = 0; k <= N; ++k) uh += gtab[G.GQ + k * Q + r] * s_B[(f * d::n1 + k) * Q * Q + pq];
+        const double df = uh - Ue[f];
+        e2 += w * df * df;
+        n2 += w * Ue[f] * Ue[f];
+      }
+    }
+  }
+  red[0][tid] = e2;
+  red[1][tid] = n2;
+  __syncthreads();
+  for (int s = nthr / 2; s > 0; s >>= 1) {
+    if (tid < s) {
+      red[0][tid] += red[0][tid + s];
+      red[1][tid] += red[1][tid + s];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    partial[2 * blockIdx.x] = red[0][0];
+    partial[2 * blockIdx.x + 1] = red[1][0];
+  }
+}
+
+}  // namespace pyrdg

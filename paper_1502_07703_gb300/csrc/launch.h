@@ -1,0 +1,30 @@
+// Type-erased launchers for one (degree, precision) pair.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace pyrdg {
+
+struct Launchers {
+  int nt;  // threads per CTA of the stage kernels
+  size_t smem_trace, smem_rhs, smem_proj, smem_err;
+  // Raise the dynamic shared-memory limit of every kernel (once per device).
+  cudaError_t (*prepare)();
+  void (*geom)(int64_t K, const double* ev, const double* gtab, void* geo, void* gface, void* invM, cudaStream_t s);
+  void (*trace)(int64_t K, const void* q, const void* tab, void* tr, cudaStream_t s);
+  void (*rhs_update)(int64_t K, void* q, void* res, const void* tr, const int32_t* mapP, const void* geo,
+                     const void* gface, const void* invM, const void* tab, int bc, double tau, double rka, double rkb,
+                     double dt, cudaStream_t s);
+  void (*rhs_out)(int64_t K, const void* q, void* rhs, const void* tr, const int32_t* mapP, const void* geo,
+                  const void* gface, const void* invM, const void* tab, int bc, double tau, cudaStream_t s);
+  void (*project)(int64_t K, const double* ev, const double* gtab, const double* tabd, int bc, double t, void* q,
+                  cudaStream_t s);
+  void (*error)(int64_t K, const void* q, const double* ev, const double* gtab, int bc, double t, double* partial,
+                int nblocks, cudaStream_t s);
+};
+
+// precision: 0 = double, 1 = float. Returns null for an unsupported degree.
+const Launchers* get_launchers(int N, int precision);
+
+}  // namespace pyrdg

@@ -1,0 +1,202 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+The two sides share only the seeded inputs (mesh, random coefficient states).
+The oracle works in the psi basis with dense matrices; the CUDA path in the
+semi-nodal basis with the diagonal mass of Lemma 3. States are compared by
+their values at every element's volume cubature points, as a
+quadrature-weighted relative L2 difference over all four fields:
+FP64 <= 1e-12, FP32 <= 1e-5 (the tolerances the target states).
+"""
+
+import numpy as np
+import pytest
+
+from oracle.dg import PyramidDG
+from paper_1502_07703_gb300.mesh import make_pyramid_mesh, random_state
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1502_07703_gb300 import build
+    build.build()
+    return torch
+
+
+def _domain(bc):
+    return (0.0, 1.0) if bc == "wall" else (-1.0, 1.0)
+
+
+def _solver(v, e, N, **kw):
+    from paper_1502_07703_gb300.binding import Solver
+    return Solver(v, e, N, **kw)
+
+
+def _rhs_case(torch, v, e, N, bc, tau, precision, seed):
+    dg = PyramidDG(v, e, N, tau=tau, bc=bc)
+    U = random_state(dg.K, dg.Np, seed)
+    with _solver(v, e, N, precision=precision, bc=bc, tau=tau) as s:
+        q = torch.tensor(U, dtype=s.torch_dtype, device="cuda")
+        R_gpu = s.rhs(q).double().cpu().numpy()
+    # the oracle gets the same input function: the coefficients as rounded to the device precision
+    Uin = U.astype(np.float32).astype(np.float64) if precision == "f32" else U
+    R_or = dg.rhs(dg.psi_from_phi(Uin))
+    return dg.rel_l2_points(dg.values_phi(R_gpu), dg.values_psi(R_or))
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
+def test_rhs_parity_all_degrees(torch_cuda, N, precision):
+    v, e = make_pyramid_mesh(3, 2, 1, delta=0.1, seed=5)
+    rel = _rhs_case(torch_cuda, v, e, N, "wall", 1.0, precision, seed=100 + N)
+    assert rel <= TOL[precision], rel
+
+
+@pytest.mark.parametrize("bc,tau", [("wall", 0.0), ("free", 1.0), ("free", 0.0), ("wall", 0.5)])
+def test_rhs_parity_flux_and_boundary_variants(torch_cuda, bc, tau):
+    v, e = make_pyramid_mesh(2, 2, 2, delta=0.08, seed=6, domain=_domain(bc))
+    rel = _rhs_case(torch_cuda, v, e, 3, bc, tau, "f64", seed=7)
+    assert rel <= TOL["f64"], rel
+
+
+def test_rhs_single_element_all_boundary(torch_cuda):
+    rng = np.random.default_rng(1)
+    ref = np.array([[-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1], [-1, -1, 1]], dtype=float)
+    v = ref + rng.uniform(-0.2, 0.2, ref.shape)
+    e = np.array([[0, 1, 2, 3, 4]], dtype=np.int32)
+    for N in (1, 4, 7):
+        rel = _rhs_case(torch_cuda, v, e, N, "wall", 1.0, "f64", seed=N)
+        assert rel <= TOL["f64"], (N, rel)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_projection_parity(torch_cuda, precision):
+    v, e = make_pyramid_mesh(3, 3, 2, delta=0.1, seed=2)
+    dg = PyramidDG(v, e, 4)
+    with _solver(v, e, 4, precision=precision) as s:
+        s.project(0.3)
+        Ug = s.get_state().astype(np.float64)
+    rel = dg.rel_l2_points(dg.values_phi(Ug), dg.values_psi(dg.project_exact(0.3)))
+    assert rel <= (1e-13 if precision == "f64" else 1e-6), rel
+
+
+def test_config1_evolution_and_error_norm(torch_cuda):
+    """48 pyramids (2x2x2 hexes, +-0.05h, seed 0), N = 3, upwind, wall, 10 LSRK4 steps at CFL 0.5."""
+    v, e = make_pyramid_mesh(2, delta=0.05, seed=0)
+    dg = PyramidDG(v, e, 3)
+    dt = dg.dt_cfl(0.5)
+    U_or = dg.lsrk4(dg.project_exact(0.0), dt, 10)
+    with _solver(v, e, 3) as s:
+        s.project(0.0)
+        s.step(10, dt)
+        Ug = s.get_state()
+        err_gpu = s.error()
+        assert abs(s.time - 10 * dt) < 1e-15
+        assert abs(s.dt_cfl(0.5) - dt) <= 1e-12 * dt
+    rel = dg.rel_l2_points(dg.values_phi(Ug), dg.values_psi(U_or))
+    assert rel <= TOL["f64"], rel
+    err_or = dg.error(U_or, 10 * dt)
+    np.testing.assert_allclose(err_gpu, err_or, rtol=1e-9)
+
+
+def test_f32_evolution_matches_oracle(torch_cuda):
+    v, e = make_pyramid_mesh(2, 2, 2, delta=0.05, seed=1)
+    N = 5
+    dg = PyramidDG(v, e, N)
+    dt = dg.dt_cfl(0.5)
+    U_or = dg.lsrk4(dg.project_exact(0.0), dt, 40)
+    with _solver(v, e, N, precision="f32") as s:
+        s.project(0.0)
+        s.step(40, dt)
+        Ug = s.get_state().astype(np.float64)
+    rel = dg.rel_l2_points(dg.values_phi(Ug), dg.values_psi(U_or))
+    assert rel <= TOL["f32"], rel
+
+
+def test_state_roundtrip_host_and_device(torch_cuda):
+    torch = torch_cuda
+    v, e = make_pyramid_mesh(2, 1, 1, delta=0.1, seed=3)
+    for prec in ("f64", "f32"):
+        with _solver(v, e, 2, precision=prec) as s:
+            U = random_state(s.K, s.Np, 4).astype(s.np_dtype)
+            s.set_state(U, t=0.25)
+            assert s.time == 0.25
+            np.testing.assert_array_equal(s.get_state(), U)
+            d = s.get_state(device=True)
+            s.set_state(d * 2, t=0.0)
+            np.testing.assert_array_equal(s.get_state(), 2 * U)
+            np.testing.assert_array_equal(d.cpu().numpy(), U)
+
+
+def _face_neighbours(EToV):
+    """Element adjacency through shared faces (test-side, from vertex sets only)."""
+    faces = ((0, 1, 2, 3), (0, 1, 4), (1, 2, 4), (3, 2, 4), (0, 3, 4))
+    owner = {}
+    nbrs = [[] for _ in range(len(EToV))]
+    for k, row in enumerate(EToV):
+        for f in faces:
+            key = tuple(sorted(int(row[i]) for i in f))
+            if key in owner:
+                j = owner.pop(key)
+                nbrs[k].append(j)
+                nbrs[j].append(k)
+            else:
+                owner[key] = k
+    return nbrs
+
+
+def _patch(nbrs, centre, radius):
+    seen = {centre: 0}
+    frontier = [centre]
+    for r in range(radius):
+        nxt = []
+        for k in frontier:
+            for j in nbrs[k]:
+                if j not in seen:
+                    seen[j] = r + 1
+                    nxt.append(j)
+        frontier = nxt
+    return sorted(seen)
+
+
+def test_full_size_config2_sampled(torch_cuda):
+    """Config of the benchmark: 32^3 hexes x 6 = 196,608 pyramids, +-0.05h (seed 1), N = 4, FP64.
+
+    (1) rhs of a random state, checked on sampled elements: the oracle runs on
+    the sample's face neighbourhood; (2) one LSRK4 step from the projected
+    standing wave, checked on sampled elements whose 6-hop neighbourhood the
+    oracle advances (influence travels one face per stage, 5 stages)."""
+    torch = torch_cuda
+    v, e = make_pyramid_mesh(32, delta=0.05, seed=1)
+    K, N = e.shape[0], 4
+    assert K == 196608
+    nbrs = _face_neighbours(e)
+    rng = np.random.default_rng(11)
+    samples = [int(x) for x in rng.choice(K, 3, replace=False)] + [0, K - 1]
+    U = random_state(K, 55, 12)
+    with _solver(v, e, N) as s:
+        R = s.rhs(torch.tensor(U, device="cuda")).cpu().numpy()
+        dt_or = PyramidDG(v, e[:6], N).dt_cfl(0.5)  # a fixed dt from one hex's pyramids
+        s.project(0.0)
+        s.step(1, dt_or)
+        U1 = s.get_state()
+    for c in samples:
+        patch = _patch(nbrs, c, 1)
+        dg = PyramidDG(v, e[patch], N)
+        i = patch.index(c)
+        Rp = dg.rhs(dg.psi_from_phi(U[patch]))
+        rel = dg.rel_l2_points(dg.values_phi(R[patch])[i:i + 1], dg.values_psi(Rp)[i:i + 1])
+        assert rel <= TOL["f64"], (c, rel)
+    for c in samples[:2]:
+        patch = _patch(nbrs, c, 6)
+        dg = PyramidDG(v, e[patch], N)
+        i = patch.index(c)
+        Up = dg.lsrk4(dg.project_exact(0.0), dt_or, 1)
+        rel = dg.rel_l2_points(dg.values_phi(U1[patch])[i:i + 1], dg.values_psi(Up)[i:i + 1])
+        assert rel <= TOL["f64"], (c, rel)

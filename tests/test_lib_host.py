@@ -1,0 +1,110 @@
+"""Host-side tests of libpyrdg.so that need no GPU: the library loads, exports
+every function include/pyrdg.h declares, its FP64 builder produces the right
+Gauss rules and face connectivity, and setup rejects bad input before any
+device work."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.special
+
+from oracle.basis import abc_to_rst
+from oracle.geometry import map_points
+from paper_1502_07703_gb300 import binding
+from paper_1502_07703_gb300.mesh import make_pyramid_mesh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1502_07703_gb300 import build
+    build.build()
+
+
+def test_exports_every_declared_symbol():
+    header = open(os.path.join(ROOT, "include", "pyrdg.h")).read()
+    names = set(re.findall(r"\b(pyr_dg_\w+)\s*\(", header))
+    assert len(names) >= 15
+    L = ctypes.CDLL(binding.LIB_PATH)
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("ab", [(0, 0), (1, 0), (2, 0), (9, 0)])
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 10])
+def test_builder_gauss_jacobi_matches_scipy(n, ab):
+    x, w = binding.gauss_jacobi(n, *ab)
+    xs, ws = scipy.special.roots_jacobi(n, *ab)
+    np.testing.assert_allclose(x, xs, atol=2e-15)
+    np.testing.assert_allclose(w, ws, rtol=2e-13)
+
+
+def _face_abc(N, face, idx):
+    """Cube coordinates of face point idx, as include/pyrdg.h documents them."""
+    n1 = N + 1
+    xg, _ = scipy.special.roots_jacobi(n1, 0, 0)
+    xf, _ = scipy.special.roots_jacobi(n1, 1, 0)
+    e, m = idx % n1, idx // n1
+    return {0: (xg[e], xg[m], -1.0), 1: (xg[e], -1.0, xf[m]), 2: (1.0, xg[e], xf[m]),
+            3: (xg[e], 1.0, xf[m]), 4: (-1.0, xg[e], xf[m])}[face]
+
+
+@pytest.mark.parametrize("N", [1, 3, 4])
+def test_connectivity_symmetric_and_coincident(N):
+    v, e = make_pyramid_mesh(3, 2, 2, delta=0.1, seed=3)
+    mapP, nb = binding.connectivity(v, e, N)
+    K = e.shape[0]
+    n2 = (N + 1) ** 2
+    Nfc = 5 * n2
+    assert nb == 2 * (3 * 2 + 3 * 2 + 2 * 2)  # hex faces on the box boundary
+    g = np.arange(K * Nfc)
+    assert np.all(mapP[mapP] == g)
+    bnd = mapP == g
+    assert bnd.sum() == nb * n2
+    # physical coordinates of every point and of its match, by the oracle's vertex map
+    abc = np.array([_face_abc(N, f, i) for f in range(5) for i in range(n2)])
+    X, _ = map_points(v[e], *abc_to_rst(abc[:, 0], abc[:, 1], abc[:, 2]))
+    X = X.reshape(-1, 3)
+    np.testing.assert_allclose(X[mapP], X, atol=1e-13)
+
+
+def test_connectivity_rejects_nonconforming_and_bad_index():
+    v, e = make_pyramid_mesh(1, delta=0.0)
+    # two pyramids glued along a triangle whose collapse vertex differs on the two sides
+    bad = e.copy()
+    bad[1] = [bad[1][4], bad[1][1], bad[1][2], bad[1][3], bad[1][0]]
+    with pytest.raises(binding.PyrDGError):
+        binding.connectivity(v, bad, 2)
+    oob = e.copy()
+    oob[0, 0] = len(v)
+    with pytest.raises(binding.PyrDGError, match="BAD_MESH"):
+        binding.connectivity(v, oob, 2)
+
+
+def test_setup_rejects_bad_input_before_device_work():
+    v, e = make_pyramid_mesh(1, delta=0.0)
+    with pytest.raises(binding.PyrDGError, match="UNSUPPORTED_N"):
+        binding.Solver(v, e, 0)
+    with pytest.raises(binding.PyrDGError, match="UNSUPPORTED_N"):
+        binding.Solver(v, e, 8)
+    inv = e.copy()
+    inv[:, [1, 3]] = inv[:, [3, 1]]  # mirror the base order: J < 0
+    with pytest.raises(binding.PyrDGError, match="BAD_MESH"):
+        binding.Solver(v, inv, 2)
+    with pytest.raises(binding.PyrDGError, match="BAD_ARG"):
+        binding.Solver(v, e, 2, tau=-1.0)
+
+
+def test_raw_abi_null_and_range_checks():
+    L = binding.lib()
+    h = ctypes.c_void_p()
+    assert L.pyr_dg_setup(None, 0, None, 0, 3, None, ctypes.byref(h)) == -1
+    assert L.pyr_dg_step(None, 1, 0.1) == -1
+    assert L.pyr_dg_error(None, None, None) == -1
+    assert b"null" in L.pyr_dg_last_error()
+    x = np.empty(4)
+    assert L.pyr_dg_host_gauss_jacobi(0, 0.0, 0.0, x.ctypes.data_as(binding._c_dp), x.ctypes.data_as(binding._c_dp)) == -1
