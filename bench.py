@@ -267,7 +267,8 @@ def main():
                 "kernel_ms_avg": rhs_ms / rhs_n, "trace_kernel_ms_avg": tr_ms / tr_n,
                 "kernel_share": rhs_ms / (rhs_ms + tr_ms)}
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers (state at t = 0 re-sent every step)
+    s.project(0.0)
     U0 = s.get_state()
     pinned = torch.from_numpy(U0).pin_memory()
     h2d = U0.nbytes
