@@ -206,6 +206,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=NX, help="hexes per axis (32 = the benchmark workload)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -223,7 +224,7 @@ def main():
     dev = local if torch.cuda.is_available() else 0
     torch.cuda.set_device(dev)
     device = torch.device("cuda", dev)
-    v, e = make_pyramid_mesh(NX, delta=DELTA, seed=SEED)
+    v, e = make_pyramid_mesh(args.nx, delta=DELTA, seed=SEED)
     s = binding.Solver(v, e, N, precision="f64", bc="wall", tau=1.0, device=dev)
     K, Np = s.K, s.Np
     dt = s.dt_cfl(0.5)
@@ -292,13 +293,14 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu, _ = oracle_sample(1, 0)
+        cpu, _ = oracle_sample(15, 1)
     line = {
         "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "K": K, "N": N, "Np": Np, "dt": dt, "step": "1 LSRK4 step = 5 RK stages",
-                   "l2_flush": "inputs larger than L2 (state 346 MB, traces 786 MB per stage, 129 MB L2)",
+        "config": {"workload": WORKLOAD if args.nx == NX else WORKLOAD.replace("32^3", f"{args.nx}^3"), "K": K, "N": N, "Np": Np, "dt": dt, "step": "1 LSRK4 step = 5 RK stages",
+                   "l2_flush": f"inputs larger than L2 (state {K * Np * 32 / 1e6:.0f} MB, traces "
+                               f"{K * 5 * (N + 1) ** 2 * 32 / 1e6:.0f} MB per stage, 129 MB L2)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks.summary(),
         "e2e": e2e,
