@@ -115,6 +115,31 @@ int pyr_dg_get_state(pyr_dg* h, void* q, int where);
  * does not touch the handle's own state. Asynchronous. */
 int pyr_dg_rhs(pyr_dg* h, const void* q_dev, void* rhs_dev);
 
+/* Allocation-free variant of pyr_dg_rhs. The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory when
+ * they call it, for example code whose device memory is all owned by another
+ * allocator (a framework's caching pool, a fixed arena) or a phase in which
+ * allocating would stall or is forbidden by the caller's own rules.
+ * Same inputs, outputs and result as pyr_dg_rhs (q_dev -> rhs_dev, device
+ * pointers of K*4*Np elements of the handle's type, no aliasing), but the face
+ * traces go to a static device array of PYR_DG_NOALLOC_SCRATCH_BYTES bytes
+ * compiled into the library instead of the handle's trace buffer. The call
+ * performs no cudaMalloc, cudaFree or other allocating routine.
+ *  - Size limit: K * Nfc * 4 * sizeof(element) must not exceed
+ *    PYR_DG_NOALLOC_SCRATCH_BYTES (8 MiB: e.g. 2097 pyramids at N = 4 in
+ *    double); larger handles get PYR_DG_ERR_BAD_ARG and a message.
+ *  - The array exists on every GPU that loads the library, until the process
+ *    exits. The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current and caches it; make that
+ *    first call before any stream capture.
+ *  - Every call shares the one array per device and it keeps the last call's
+ *    contents. Each call writes every entry it reads before reading it, so
+ *    nothing needs clearing, but calls whose work overlaps on the GPU (other
+ *    streams, other handles, other threads) race on it: serialise them.
+ * Asynchronous, on the handle's stream. */
+enum { PYR_DG_NOALLOC_SCRATCH_BYTES = 8 << 20 };
+int pyr_dg_rhs_noalloc(pyr_dg* h, const void* q_dev, void* rhs_dev);
+
 /* Advance the handle's state nsteps LSRK4 steps of size dt (> 0); each step
  * is 5 stages, each stage one trace launch and one fused
  * volume + flux + lift + M^{-1} + update launch. Advances the time by

@@ -66,6 +66,7 @@ _SIGNATURES = {
     "pyr_dg_host_connectivity": (ctypes.c_int, [_c_dp, ctypes.c_int64, _c_i32p, ctypes.c_int64, ctypes.c_int,
                                                 _c_i64p, _c_i64p]),
     "pyr_dg_fma_peak": (ctypes.c_int, [ctypes.c_int, _c_dp]),
+    "pyr_dg_rhs_noalloc": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_void_p]),
     "pyr_dg_profile": (ctypes.c_int, [_c_h, ctypes.c_int]),
     "pyr_dg_profile_read": (ctypes.c_int, [_c_h, _c_dp, _c_i64p, _c_dp, _c_i64p]),
 }

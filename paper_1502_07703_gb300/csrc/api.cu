@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -464,3 +465,46 @@ void pyr_dg_destroy(pyr_dg* h) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------
+// pyr_dg_rhs_noalloc: the trace scratch of pyr_dg_rhs in a static device array.
+namespace {
+constexpr int kMaxNoallocDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PYR_DG_NOALLOC_SCRATCH_BYTES];
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxNoallocDevices] = {};
+}  // namespace
+
+extern "C" int pyr_dg_rhs_noalloc(pyr_dg* h, const void* q_dev, void* rhs_dev) {
+  if (!h || !q_dev || !rhs_dev) return fail(PYR_DG_ERR_BAD_ARG, "null argument");
+  if (q_dev == rhs_dev) return fail(PYR_DG_ERR_BAD_ARG, "rhs must not alias q");
+  const size_t need = (size_t)h->K * h->Nfc * 4 * h->tsize;
+  if (need > (size_t)PYR_DG_NOALLOC_SCRATCH_BYTES)
+    return fail(PYR_DG_ERR_BAD_ARG,
+                "pyr_dg_rhs_noalloc: this mesh needs %zu bytes of face-trace scratch (K=%lld, Nfc=%d, 4 fields, "
+                "%zu-byte elements) but the static scratch holds %d bytes; use pyr_dg_rhs",
+                need, (long long)h->K, h->Nfc, h->tsize, (int)PYR_DG_NOALLOC_SCRATCH_BYTES);
+  if (h->device < 0 || h->device >= kMaxNoallocDevices)
+    return fail(PYR_DG_ERR_BAD_ARG, "pyr_dg_rhs_noalloc supports device ordinals below %d", kMaxNoallocDevices);
+  DeviceGuard g(h->device);
+  CUDA_TRY(g.err);
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[h->device]) {
+      // host code sees only a stand-in for the array: fetch its device address once per device
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess)
+        return fail(PYR_DG_ERR_CUDA, "cudaGetSymbolAddress(scratch) on device %d: %s", h->device,
+                    cudaGetErrorString(e));
+      g_noalloc_addr[h->device] = p;
+    }
+    scratch = g_noalloc_addr[h->device];
+  }
+  h->L->trace(h->K, q_dev, h->tab, scratch, h->stream);
+  h->L->rhs_out(h->K, q_dev, rhs_dev, scratch, h->mapP, h->geo, h->gface, h->invM, h->tab, h->bc, h->tau,
+                h->stream);
+  CUDA_TRY(cudaGetLastError());
+  return PYR_DG_OK;
+}
