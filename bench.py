@@ -50,24 +50,22 @@ def num_modes(n):
 def rhs_flops_per_element(n):
     """Algorithmic FP64 flops of the fused stage kernel per element (sum-factorised).
 
-    Counts every multiply-add as 2 flops, following the kernel's passes:
-    a pass (A, dA), b pass (U, U_a, U_b), c pass + chain rule, face flux,
-    c^T pass with base and triangle faces, b^T and a^T passes, M^{-1} and the
-    LSRK update."""
+    Counts a multiply-add as 2 flops, following the kernel's passes: a pass
+    (A, dA), b pass (U, U_a, U_b), per-level combination of the three velocity
+    fields for div(u), level mixing of the c direction (MH, MG) with the chain
+    rule and the base-face lift, triangle-face c^T pass, b^T and a^T passes,
+    face flux, M^{-1} and the LSRK update."""
     n1, n2, P3 = n + 1, (n + 1) ** 2, n + 3
-    Np, nrow, Nc, Nfc = num_modes(n), n1 * (n1 + 1) // 2, n1 ** 3, 5 * n2
+    Np, nrow, Nfc = num_modes(n), n1 * (n1 + 1) // 2, 5 * n2
     sum_k1 = n1 * (n1 + 1) // 2  # sum_k (k+1)
-    mac = 0
-    mac += 4 * n1 * 2 * Np                      # a pass: 2 outputs, (k+1) terms, per (f, k, j, p)
+    mac = 4 * n1 * 2 * Np                       # a pass: 2 outputs, (k+1) terms, per (f, k, j, p)
     mac += 4 * n2 * 3 * sum_k1                  # b pass: 3 outputs per (f, k, pq), (k+1) terms
-    mac += Nc * (12 * n1 + 18)                  # c pass (3 sums x 4 fields) + chain rule
-    flops = 2 * mac + Nc * (4 + 2)              # wc scaling (4 mults) + div sum (2 adds)
-    flops += Nfc * 26                           # flux at face points
-    mac = 4 * n1 * (n2 * n1 + n2 + 4 * n1 * n1)  # c^T pass incl. base and triangle faces
+    mac += n1 * n2 * 9                          # div combination per (k, pq)
+    mac += n1 * n2 * (5 * n1 + 13)              # level mixing + chain rule + base lift per (k', pq)
+    mac += 16 * n1 * n1 * n1                    # triangle-face c^T
     mac += 4 * nrow * (n1 * P3 + 2 * n1)        # b^T pass
     mac += 4 * Np * P3                          # a^T pass
-    flops += 2 * mac + 4 * Np * 5               # M^{-1} (1), LSRK (2 FMA = 4)
-    return flops
+    return 2 * mac + Nfc * 26 + 4 * Np * 5      # flux per face point; M^{-1} (1) and LSRK (2 FMA)
 
 
 def trace_flops_per_element(n):
@@ -261,7 +259,11 @@ def main():
     peak = binding.fma_peak("f64")
     rhs_avg_s = rhs_ms / rhs_n * 1e-3
     achieved = rhs_flops_per_element(N) * K / rhs_avg_s / 1e12
-    traffic = None
+    # DRAM bytes per element of the fused stage kernel, from the ncu capture summarised in
+    # profiles/rhs_kernel_n4_f64_24cube.md (82,944 pyramids, N = 4, FP64: 1196.3 MB read +
+    # write per launch); traffic scales with the element count. Valid for that kernel
+    # version only: reset to None when the kernel changes, until it is measured again.
+    traffic = 14423.0 * K if (N == 4 and args.nx >= 24) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "rhs_kernel<4,double,update>",
                 "peak_kind": "FP64 FMA throughput measured in this run (nominal 1.25)",

@@ -162,6 +162,19 @@ int build_tables(int N, RefTables& t) {
         t.geo[G.IMR + lvl_off(k) + j * (k + 1) + i] = 1.0 / (wk[i] * wk[j] * Ck[k]);
   }
   for (int r = 0; r < n1; ++r) t.tab[L.WC + r] = 0.25 * wc[r];
+  // The volume geometric factors do not depend on c, so the c-interpolation of
+  // derivatives and the c-projection onto level k' collapse into these sums.
+  for (int kp = 0; kp <= N; ++kp)
+    for (int k = 0; k <= N; ++k) {
+      double mh = 0.0, mg = 0.0;
+      for (int r = 0; r < n1; ++r) {
+        const double w = 0.25 * wc[r] * t.tab[L.GC + kp * n1 + r];
+        mh += w * t.tab[L.HC + k * n1 + r];
+        mg += w * t.tab[L.DGC + k * n1 + r];
+      }
+      t.tab[L.MH + kp * n1 + k] = mh;
+      t.tab[L.MG + kp * n1 + k] = mg;
+    }
   for (int q = 0; q < n1; ++q)
     for (int p = 0; p < n1; ++p) {
       t.tab[L.WB + p + n1 * q] = wg[p] * wg[q];

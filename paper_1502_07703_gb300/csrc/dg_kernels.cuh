@@ -74,20 +74,26 @@ __device__ __forceinline__ double d_jacobian(const double* v, double a, double b
   return Ba[0] * g1[0] + Ba[1] * g1[1] + Ba[2] * g1[2];
 }
 
-// Exact standing waves (wall on [0,1]^3, free surface on [-1,1]^3).
-__device__ __forceinline__ void d_exact(int bc, double x, double y, double z, double t, double* out) {
-  const double k = bc == 0 ? 3.14159265358979323846 : 1.57079632679489661923;
-  const double s3 = 1.7320508075688772935;
-  const double om = s3 * k;
-  double sx, cx, sy, cy, sz, cz, st, ct;
-  sincos(k * x, &sx, &cx);
-  sincos(k * y, &sy, &cy);
-  sincos(k * z, &sz, &cz);
-  sincos(om * t, &st, &ct);
-  out[0] = cx * cy * cz * ct;
-  out[1] = sx * cy * cz * st / s3;
-  out[2] = cx * sy * cz * st / s3;
-  out[3] = cx * cy * sz * st / s3;
+// Exact standing waves (wall on [0,1]^3, free surface on [-1,1]^3). The spatial
+// factors are cos/sin(pi s x) with s = 1 (wall) or 1/2 (free), evaluated with
+// sincospi; ct, st = cos, sin(sqrt(3) pi s t) come from the caller once per launch.
+__device__ __forceinline__ void d_exact(int bc, double x, double y, double z, double ct, double st, double* out) {
+  const double sc = bc == 0 ? 1.0 : 0.5;
+  const double inv_s3 = 0.57735026918962576451;
+  double sx, cx, sy, cy, sz, cz;
+  sincospi(sc * x, &sx, &cx);
+  sincospi(sc * y, &sy, &cy);
+  sincospi(sc * z, &sz, &cz);
+  const double cyz = cy * cz;
+  out[0] = cx * cyz * ct;
+  out[1] = sx * cyz * (st * inv_s3);
+  out[2] = cx * sy * cz * (st * inv_s3);
+  out[3] = cx * cy * sz * (st * inv_s3);
+}
+
+__device__ __forceinline__ void d_time_factors(int bc, double t, double* ct, double* st) {
+  const double sc = bc == 0 ? 1.0 : 0.5;
+  sincospi(1.7320508075688772935 * sc * t, st, ct);
 }
 
 // ============================================================ geometry (a1)
@@ -183,25 +189,27 @@ __global__ void __launch_bounds__(KCfg<N>::NT) trace_kernel(int64_t K, const T* 
   for (int x = tid; x < L.size; x += blockDim.x) s_tab[x] = tab[x];
   for (int x = tid; x < 4 * d::Np; x += blockDim.x) s_u[x] = q[e * 4 * d::Np + x];
   __syncthreads();
-  // a pass: A[f][row(k,j)][p'] = sum_i l_i^k(x_p') u[f][k][j][i], p' over GL points and -1, +1
+  // a pass: A[f][row(k,j)][p'] = sum_i l_i^k(x_p') u[f][k][j][i], p' over GL points and -1, +1.
+  // Work items run level-major so that a warp's lanes share the trip count k+1.
   for (int x = tid; x < 4 * d::nrow * d::P3; x += blockDim.x) {
-    const int pp = x % d::P3;
-    const int t = x / d::P3;
-    const int row = t % d::nrow, f = t / d::nrow;
-    int k, j;
-    decode_row(row, k, j);
+    int k = 0;
+    while (x >= 4 * d::P3 * tri_num(k + 1)) ++k;
+    const int rem = x - 4 * d::P3 * tri_num(k);
+    const int f = rem / ((k + 1) * d::P3);
+    const int j = (rem / d::P3) % (k + 1);
+    const int pp = rem % d::P3;
     const T* uc = s_u + f * d::Np + lvl_off(k) + j * (k + 1);
     const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + pp;
     T acc = 0;
     for (int i = 0; i <= k; ++i) acc += uc[i] * lx[i * d::P3];
-    s_A[x] = acc;
+    s_A[(f * d::nrow + tri_num(k) + j) * d::P3 + pp] = acc;
   }
   __syncthreads();
   // b pass per level k: base grid (p,q) and the four triangle-face rows
   for (int x = tid; x < 4 * d::n1 * S::nB; x += blockDim.x) {
     const int s = x % S::nB;
     const int t = x / S::nB;
-    const int k = t % d::n1, f = t / d::n1;
+    const int f = t % 4, k = t / 4;  // level-major: equal trip counts within a warp
     int pa, qb;  // A column (a point) and l^k_j evaluation column (b point)
     if (s < d::n2) {
       pa = s % d::n1;
@@ -221,7 +229,7 @@ __global__ void __launch_bounds__(KCfg<N>::NT) trace_kernel(int64_t K, const T* 
     const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + qb;
     T acc = 0;
     for (int j = 0; j <= k; ++j) acc += Ar[j * d::P3] * lx[j * d::P3];
-    s_B[x] = acc;
+    s_B[(f * d::n1 + k) * S::nB + s] = acc;
   }
   __syncthreads();
   // c pass: sum over levels with G_k(-1) (base) or G_k(c_m) (triangles)
@@ -267,13 +275,15 @@ struct RhsSmem {
   static constexpr size_t U = dA + 4 * d::nrow * d::n1;
   static constexpr size_t Ua = U + 4 * d::n1 * d::n2;
   static constexpr size_t Ub = Ua + 4 * d::n1 * d::n2;
-  // after the c pass U/Ua/Ub are dead: Y and Z reuse their space
-  static constexpr size_t Y = U;
-  static constexpr size_t Z = Y + 4 * d::n1 * nY;
-  static constexpr size_t R1 = 3 * 4 * d::n1 * d::n2;
-  static constexpr size_t R2 = 4 * d::n1 * nY + 4 * d::nrow * d::P3;
-  static constexpr size_t Fv = U + (R1 > R2 ? R1 : R2);
-  static constexpr size_t total = Fv + 4 * d::Nc;
+  static constexpr size_t Y = Ub + 4 * d::n1 * d::n2;
+  static constexpr size_t total = Y + 4 * d::n1 * nY;
+  // A/dA are dead after the b pass: the div combination X, Z and later the
+  // b^T output reuse their space.
+  static constexpr size_t X = A;
+  static constexpr size_t Zc = X + d::n1 * d::n2;
+  static constexpr size_t Zb = A;
+  static_assert(2 * d::n1 * d::n2 <= 8 * d::nrow * d::n1, "X/Z overflow the A region");
+  static_assert(4 * d::nrow * d::P3 <= 8 * d::nrow * d::n1, "b^T output overflows the A region");
   static constexpr size_t bytes = total * sizeof(T);
 };
 
@@ -376,6 +386,7 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
   using d = Dims<N>;
   using S = RhsSmem<N, T>;
   constexpr TabLayout L(N);
+  constexpr int nY = S::nY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   T* s_tab = sm + S::tab;
@@ -388,9 +399,10 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
   T* s_U = sm + S::U;
   T* s_Ua = sm + S::Ua;
   T* s_Ub = sm + S::Ub;
-  T* s_Fv = sm + S::Fv;
   T* s_Y = sm + S::Y;
-  T* s_Z = sm + S::Z;
+  T* s_X = sm + S::X;
+  T* s_Zc = sm + S::Zc;
+  T* s_Zb = sm + S::Zb;
   const int64_t e = blockIdx.x;
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
@@ -418,13 +430,14 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
 #pragma unroll
     for (int f = 0; f < 4; ++f) s_Fs[f * d::Nfc + g] = F[f];
   }
-  // a pass: A = l(a_p) u, dA = l'(a_p) u
+  // a pass, level-major: A = l^k(a_p) u, dA = l^k'(a_p) u
   for (int x = tid; x < 4 * d::nrow * d::n1; x += nthr) {
-    const int p = x % d::n1;
-    const int t = x / d::n1;
-    const int row = t % d::nrow, f = t / d::nrow;
-    int k, j;
-    decode_row(row, k, j);
+    int k = 0;
+    while (x >= 4 * d::n1 * tri_num(k + 1)) ++k;
+    const int rem = x - 4 * d::n1 * tri_num(k);
+    const int f = rem / ((k + 1) * d::n1);
+    const int j = (rem / d::n1) % (k + 1);
+    const int p = rem % d::n1;
     const T* uc = s_u + f * d::Np + lvl_off(k) + j * (k + 1);
     const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + p;
     const T* dl = s_tab + L.DL + tri_num(k) * d::n1 + p;
@@ -433,15 +446,16 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
       a += uc[i] * lx[i * d::P3];
       da += uc[i] * dl[i * d::n1];
     }
-    s_A[x] = a;
-    s_dA[x] = da;
+    const int o = (f * d::nrow + tri_num(k) + j) * d::n1 + p;
+    s_A[o] = a;
+    s_dA[o] = da;
   }
   __syncthreads();
-  // b pass: U_k, (d_a U)_k, (d_b U)_k on the (a_p, b_q) grid
+  // b pass, level-major: U_k, (d_a U)_k, (d_b U)_k on the (a_p, b_q) grid
   for (int x = tid; x < 4 * d::n1 * d::n2; x += nthr) {
     const int pq = x % d::n2;
     const int t = x / d::n2;
-    const int k = t % d::n1, f = t / d::n1;
+    const int f = t % 4, k = t / 4;
     const int p = pq % d::n1, q = pq / d::n1;
     const T* Ar = s_A + (f * d::nrow + tri_num(k)) * d::n1 + p;
     const T* dAr = s_dA + (f * d::nrow + tri_num(k)) * d::n1 + p;
@@ -454,56 +468,108 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
       ub += av * dl[j * d::n1];
       ua += dAr[j * d::n1] * lv;
     }
-    s_U[x] = u;
-    s_Ua[x] = ua;
-    s_Ub[x] = ub;
+    const int o = (f * d::n1 + k) * d::n2 + pq;
+    s_U[o] = u;
+    s_Ua[o] = ua;
+    s_Ub[o] = ub;
   }
   __syncthreads();
-  // c pass + chain rule (Alg. 1): weighted J div(u) and J grad(p) at the volume points
-  for (int x = tid; x < d::Nc; x += nthr) {
-    const int pq = x % d::n2, r = x / d::n2;
-    const T* hc = s_tab + L.HC + r;
-    const T* dg = s_tab + L.DGC + r;
-    T d3[4][3];
+  // div(u) needs only sum_m J d(u_m)/dx_m = sum_m (u_r^m g1_m + u_s^m g2_m + u_c^m g3_m); the
+  // factors do not depend on c, so combine the fields per level before the c direction.
+  for (int x = tid; x < d::n1 * d::n2; x += nthr) {
+    const int pq = x % d::n2, k = x / d::n2;
+    const T* g = s_geo + pq * d::NGEO;
+    T xs = 0, zs = 0;
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      const T* Uf = s_U + f * d::n1 * d::n2 + pq;
-      const T* Uaf = s_Ua + f * d::n1 * d::n2 + pq;
-      const T* Ubf = s_Ub + f * d::n1 * d::n2 + pq;
-      T ur = 0, us = 0, uc = 0;
+    for (int m = 0; m < 3; ++m) {
+      const int o = ((m + 1) * d::n1 + k) * d::n2 + pq;
+      xs += g[m] * s_Ua[o] + g[3 + m] * s_Ub[o];
+      zs += g[6 + m] * s_U[o];
+    }
+    s_X[x] = xs;
+    s_Zc[x] = zs;
+  }
+  __syncthreads();
+  // c direction of the volume term (Alg. 1) as level mixing: the projection onto level k'
+  // of the weighted derivatives, sum_r WC G_k'(c_r) (...)(c_r), is MH / MG applied to the
+  // level values at each (a_p, b_q). Base-face lift (c = -1) joins here; the triangle
+  // faces fill the extra rows/columns of Y.
+  for (int x = tid; x < d::n1 * d::n2 + 4 * d::n1 * 4 * d::n1; x += nthr) {
+    if (x < d::n1 * d::n2) {
+      const int pq = x % d::n2, kp = x / d::n2;
+      const int p = pq % d::n1, q = pq / d::n1;
+      const T* mh = s_tab + L.MH + kp * d::n1;
+      const T* mg = s_tab + L.MG + kp * d::n1;
+      T al = 0, be = 0, ga = 0, dv = 0;
 #pragma unroll
       for (int k = 0; k <= N; ++k) {
-        ur += hc[k * d::n1] * Uaf[k * d::n2];
-        us += hc[k * d::n1] * Ubf[k * d::n2];
-        uc += dg[k * d::n1] * Uf[k * d::n2];
+        const int o = k * d::n2 + pq;  // field 0 (p)
+        al += mh[k] * s_Ua[o];
+        be += mh[k] * s_Ub[o];
+        ga += mg[k] * s_U[o];
+        dv += mh[k] * s_X[o] + mg[k] * s_Zc[o];
       }
-      d3[f][0] = ur;
-      d3[f][1] = us;
-      d3[f][2] = uc;
+      const T* g = s_geo + pq * d::NGEO;
+      const T gb = s_tab[L.GB + kp];
+      const int yo = kp * nY + p * d::P3 + q;
+      s_Y[0 * d::n1 * nY + yo] = dv + gb * s_Fs[0 * d::Nfc + pq];
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+        s_Y[(m + 1) * d::n1 * nY + yo] =
+            g[m] * al + g[3 + m] * be + g[6 + m] * ga + gb * s_Fs[(m + 1) * d::Nfc + pq];
+    } else {
+      const int y = x - d::n1 * d::n2;
+      const int ee = y % d::n1;
+      const int slot = (y / d::n1) % 4;
+      const int f = (y / (4 * d::n1)) % 4;
+      const int k = y / (16 * d::n1);
+      const int face = slot == 0 ? 1 : slot == 1 ? 3 : slot == 2 ? 4 : 2;
+      const T* fs = s_Fs + f * d::Nfc + face * d::n2 + ee;
+      const T* gfk = s_tab + L.GF + k * d::n1;
+      T acc = 0;
+#pragma unroll
+      for (int m = 0; m <= N; ++m) acc += gfk[m] * fs[m * d::n1];
+      T* Yk = s_Y + (f * d::n1 + k) * nY;
+      if (slot < 2)
+        Yk[ee * d::P3 + d::n1 + slot] = acc;  // b = -1, +1 columns
+      else
+        Yk[(d::n1 + slot - 2) * d::P3 + ee] = acc;  // a = -1, +1 rows
     }
-    const T* g = s_geo + pq * d::NGEO;  // w_p w_q (g1, g2, g3)
-    const T wc = s_tab[L.WC + r];
-    const T px = d3[0][0] * g[0] + d3[0][1] * g[3] + d3[0][2] * g[6];
-    const T py = d3[0][0] * g[1] + d3[0][1] * g[4] + d3[0][2] * g[7];
-    const T pz = d3[0][0] * g[2] + d3[0][1] * g[5] + d3[0][2] * g[8];
-    const T ux = d3[1][0] * g[0] + d3[1][1] * g[3] + d3[1][2] * g[6];
-    const T vy = d3[2][0] * g[1] + d3[2][1] * g[4] + d3[2][2] * g[7];
-    const T wz = d3[3][0] * g[2] + d3[3][1] * g[5] + d3[3][2] * g[8];
-    s_Fv[0 * d::Nc + x] = wc * (ux + vy + wz);
-    s_Fv[1 * d::Nc + x] = wc * px;
-    s_Fv[2 * d::Nc + x] = wc * py;
-    s_Fv[3 * d::Nc + x] = wc * pz;
   }
   __syncthreads();
-  // projections: volume (V^T) and lift ((V^f)^T) in the same transposed passes
-  project_passes<N, T>(s_tab, s_Fv, s_Fs, s_Y, s_Z, tid, nthr);
+  // b^T pass: Z[f][row(k,j)][p'] = sum_q' l_j^k(x_q') Y[f][k][p'][q']; the items with
+  // p' on the (a) grid sum N+3 terms, the two face rows N+1 terms; they are kept apart.
+  constexpr int nMain = 4 * d::nrow * d::n1;
+  for (int x = tid; x < 4 * d::nrow * d::P3; x += nthr) {
+    int row, f, pp, nq;
+    if (x < nMain) {
+      pp = x % d::n1;
+      f = (x / d::n1) % 4;
+      row = x / (4 * d::n1);
+      nq = d::P3;
+    } else {
+      const int y = x - nMain;
+      pp = d::n1 + y % 2;
+      f = (y / 2) % 4;
+      row = y / 8;
+      nq = d::n1;
+    }
+    int k, j;
+    decode_row(row, k, j);
+    const T* Yr = s_Y + ((f * d::n1 + k) * d::P3 + pp) * d::P3;
+    const T* lx = s_tab + L.LX + (tri_num(k) + j) * d::P3;
+    T acc = 0;
+    for (int q = 0; q < nq; ++q) acc += lx[q] * Yr[q];
+    s_Zb[(f * d::nrow + row) * d::P3 + pp] = acc;
+  }
+  __syncthreads();
   // a^T pass, M^{-1} (a6), LSRK stage (a7)
   for (int x = tid; x < 4 * d::Np; x += nthr) {
     const int f = x / d::Np, n = x % d::Np;
     int k, j, i;
     decode_mode(n, k, j, i);
     const T* lx = s_tab + L.LX + (tri_num(k) + i) * d::P3;
-    const T* Zr = s_Z + (f * d::nrow + tri_num(k) + j) * d::P3;
+    const T* Zr = s_Zb + (f * d::nrow + tri_num(k) + j) * d::P3;
     T acc = 0;
 #pragma unroll
     for (int pp = 0; pp < d::P3; ++pp) acc += lx[pp] * Zr[pp];
@@ -553,6 +619,8 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
   for (int x = tid; x < L.size; x += nthr) s_tab[x] = tabd[x];
   if (tid < 15) v[tid] = ev[e * 15 + tid];
   __syncthreads();
+  double ct, st;
+  d_time_factors(bc, t, &ct, &st);
   for (int x = tid; x < d::Nc; x += nthr) {
     const int pq = x % d::n2, r = x / d::n2;
     const int p = pq % d::n1, q = pq / d::n1;
@@ -561,7 +629,7 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
     d_bilinear(v, a, b, B, Ba, Bb);
     for (int m = 0; m < 3; ++m) X[m] = 0.5 * (1 - c) * B[m] + 0.5 * (1 + c) * v[12 + m];
     const double w = gtab[G.WG + p] * gtab[G.WG + q] * gtab[G.WC4 + r] * d_jacobian(v, a, b);
-    d_exact(bc, X[0], X[1], X[2], t, U);
+    d_exact(bc, X[0], X[1], X[2], ct, st, U);
     for (int f = 0; f < 4; ++f) s_Fv[f * d::Nc + x] = w * U[f];
   }
   __syncthreads();
@@ -610,6 +678,8 @@ __global__ void __launch_bounds__(256)
   __shared__ double red[2][256];
   const int tid = threadIdx.x, nthr = blockDim.x;
   double e2 = 0.0, n2 = 0.0;
+  double ct, st;
+  d_time_factors(bc, t, &ct, &st);
   for (int64_t e = blockIdx.x; e < K; e += gridDim.x) {
     __syncthreads();
     for (int x = tid; x < 4 * d::Np; x += nthr) s_u[x] = (double)q[e * 4 * d::Np + x];
@@ -646,7 +716,7 @@ __global__ void __launch_bounds__(256)
       d_bilinear(v, a, b, B, Ba, Bb);
       for (int m = 0; m < 3; ++m) X[m] = 0.5 * (1 - c) * B[m] + 0.5 * (1 + c) * v[12 + m];
       const double w = gtab[G.WQ + p] * gtab[G.WQ + qq] * gtab[G.WQC + r] * d_jacobian(v, a, b);
-      d_exact(bc, X[0], X[1], X[2], t, Ue);
+      d_exact(bc, X[0], X[1], X[2], ct, st, Ue);
       for (int f = 0; f < 4; ++f) {
         double uh = 0;
         for (int k = 0; k <= N; ++k) uh += gtab[G.GQ + k * Q + r] * s_B[(f * d::n1 + k) * Q * Q + pq];

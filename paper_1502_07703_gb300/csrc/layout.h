@@ -42,7 +42,7 @@ struct Dims {
 
 // Precision-typed operator tables (one contiguous array per degree).
 struct TabLayout {
-  int LX, DL, GC, DGC, HC, GB, GF, WC, WB, WFT, size;
+  int LX, DL, GC, DGC, HC, GB, GF, WC, WB, WFT, MH, MG, size;
   PYR_HD constexpr TabLayout(int N)
       : LX(0),
         DL(LX + tri_num(N + 1) * (N + 3)),
@@ -54,7 +54,9 @@ struct TabLayout {
         WC(GF + (N + 1) * (N + 1)),
         WB(WC + (N + 1)),
         WFT(WB + (N + 1) * (N + 1)),
-        size(WFT + (N + 1) * (N + 1)) {}
+        MH(WFT + (N + 1) * (N + 1)),
+        MG(MH + (N + 1) * (N + 1)),
+        size(MG + (N + 1) * (N + 1)) {}
 };
 // LX[(tri(k)+i)*P3 + p]  = l_i^k(x_p), x_p: GL points p<=N, then -1, +1
 // DL[(tri(k)+i)*n1 + p]  = l_i^k'(x_p), p <= N
@@ -64,6 +66,8 @@ struct TabLayout {
 // WC[r]                  = GJ(2,0) weight / 4  (Duffy factor ((1-c)/2)^2)
 // WB[p + n1 q]           = w_p w_q (base face)
 // WFT[e + n1 m]          = w_e * GJ(1,0) weight / 2 (triangle faces)
+// MH[k'*n1 + k]          = sum_r WC[r] G_{k'}(c_r) H_k(c_r)    (the c direction of the
+// MG[k'*n1 + k]          = sum_r WC[r] G_{k'}(c_r) G_k'(c_r)   volume term as level mixing)
 
 // Double tables for geometry, mass diagonal, projection and error rule.
 struct GeoLayout {
