@@ -197,6 +197,41 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def measure_form(binding, nx, delta, seed, n, precision, steps, warmup, dev):
+    """Device-timed LSRK4 steps of one (mesh, degree, precision) form, plus the L2 error
+    against the exact solution after warmup + steps steps from the projected standing wave."""
+    import torch
+    from paper_1502_07703_gb300.mesh import make_pyramid_mesh
+
+    v, e = make_pyramid_mesh(nx, delta=delta, seed=seed)
+    s = binding.Solver(v, e, n, precision=precision, bc="wall", tau=1.0, device=dev)
+    dt = s.dt_cfl(0.5)
+    s.project(0.0)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(warmup):
+        s.step(1, dt)
+    s.sync()
+    s.profile(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        s.step(1, dt)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    prof = s.profile_read()
+    s.profile(False)
+    err_abs, err_rel = s.error()
+    out = {"mesh": f"{nx}^3 hexes x 6, +-{delta}h (seed {seed})", "K": s.K, "N": n, "Np": s.Np,
+           "precision": precision, "steps": steps, "ms_per_step": ms / steps,
+           "dof_updates_per_s_per_stage": s.K * s.Np * 4 * 5 * steps / (ms * 1e-3),
+           "rhs_kernel_ms": prof["rhs"][0] / prof["rhs"][1], "trace_kernel_ms": prof["trace"][0] / prof["trace"][1],
+           "l2_rel_error_vs_exact": err_rel, "t_end": (warmup + steps) * dt}
+    s.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -204,6 +239,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP32 precision-form measurements")
     ap.add_argument("--nx", type=int, default=NX, help="hexes per axis (32 = the benchmark workload)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -293,6 +329,13 @@ def main():
            "includes": "H2D of the state from pinned memory + 1 LSRK4 step + L2 error norm (double) + D2H"}
     err_abs, err_rel = s.error()
 
+    forms = []
+    if not args.no_forms:
+        s.close()
+        for nx, delta, seed, n, prec, st in ((NX, DELTA, SEED, 4, "f32", 20), (NX, DELTA, SEED, 5, "f32", 20),
+                                             (NX, DELTA, SEED, 7, "f32", 10), (64, 0.1, 3, 5, "f32", 10)):
+            forms.append(measure_form(binding, nx, delta, seed, n, prec, st, 2, dev))
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu, _ = oracle_sample(15, 1)
@@ -310,10 +353,12 @@ def main():
         "roofline": roofline,
         "cpu_baseline": cpu,
         "l2_error_vs_exact": {"abs": err_abs, "rel": err_rel},
+        "precision_forms": forms,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    s.close()
+    if args.no_forms:
+        s.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -621,14 +621,26 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
   __syncthreads();
   double ct, st;
   d_time_factors(bc, t, &ct, &st);
+  // B(a,b) and w_p w_q J(a,b) once per (a,b) point, parked in the Y region until the c^T pass
+  double* s_XB = s_Y;
+  for (int pq = tid; pq < d::n2; pq += nthr) {
+    const int p = pq % d::n1, q = pq / d::n1;
+    const double a = gtab[G.XG + p], b = gtab[G.XG + q];
+    double B[3], Ba[3], Bb[3];
+    d_bilinear(v, a, b, B, Ba, Bb);
+    s_XB[4 * pq + 0] = B[0];
+    s_XB[4 * pq + 1] = B[1];
+    s_XB[4 * pq + 2] = B[2];
+    s_XB[4 * pq + 3] = gtab[G.WG + p] * gtab[G.WG + q] * d_jacobian(v, a, b);
+  }
+  __syncthreads();
   for (int x = tid; x < d::Nc; x += nthr) {
     const int pq = x % d::n2, r = x / d::n2;
-    const int p = pq % d::n1, q = pq / d::n1;
-    const double a = gtab[G.XG + p], b = gtab[G.XG + q], c = gtab[G.XC + r];
-    double B[3], Ba[3], Bb[3], X[3], U[4];
-    d_bilinear(v, a, b, B, Ba, Bb);
-    for (int m = 0; m < 3; ++m) X[m] = 0.5 * (1 - c) * B[m] + 0.5 * (1 + c) * v[12 + m];
-    const double w = gtab[G.WG + p] * gtab[G.WG + q] * gtab[G.WC4 + r] * d_jacobian(v, a, b);
+    const double c = gtab[G.XC + r];
+    const double* xb = s_XB + 4 * pq;
+    double X[3], U[4];
+    for (int m = 0; m < 3; ++m) X[m] = 0.5 * (1 - c) * xb[m] + 0.5 * (1 + c) * v[12 + m];
+    const double w = xb[3] * gtab[G.WC4 + r];
     d_exact(bc, X[0], X[1], X[2], ct, st, U);
     for (int f = 0; f < 4; ++f) s_Fv[f * d::Nc + x] = w * U[f];
   }
@@ -649,7 +661,16 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
 
 // ============================================================ error norm (a8)
 // sum over elements and (N+3)^3 points of w J |U_h - U_exact|^2 and w J |U_exact|^2,
-// in double; grid-stride over elements, one partial pair per block.
+// in double; grid-stride over elements, one partial pair per block. The base map
+// B(a,b) and J(a,b) do not depend on c, so they are computed once per (a,b) point.
+template <int N>
+struct ErrCfg {
+  static constexpr int Q = N + 3;
+  static constexpr int pts = Q * Q * Q;
+  static constexpr int iters = (pts + 511) / 512;
+  static constexpr int NT = (((pts + iters - 1) / iters) + 31) / 32 * 32;
+};
+
 template <int N>
 struct ErrSmem {
   using d = Dims<N>;
@@ -657,26 +678,35 @@ struct ErrSmem {
   static constexpr size_t u = 0;
   static constexpr size_t A = u + 4 * d::Np;
   static constexpr size_t B = A + 4 * d::nrow * Q;
-  static constexpr size_t total = B + 4 * d::n1 * Q * Q;
+  static constexpr size_t LQ = B + 4 * d::n1 * Q * Q;
+  static constexpr size_t GQ = LQ + d::nrow * Q;
+  static constexpr size_t XB = GQ + d::n1 * Q;  // per (a,b) point: B(a,b) and w_p w_q J(a,b)
+  static constexpr size_t total = XB + 4 * Q * Q;
   static constexpr size_t bytes = total * sizeof(double);
 };
 
 template <int N, typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(ErrCfg<N>::NT)
     error_kernel(int64_t K, const T* __restrict__ q, const double* __restrict__ ev, const double* __restrict__ gtab,
                  int bc, double t, double* __restrict__ partial) {
   using d = Dims<N>;
   using S = ErrSmem<N>;
   constexpr GeoLayout G(N);
   constexpr int Q = d::Q;
+  constexpr int NW = ErrCfg<N>::NT / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* sm = reinterpret_cast<double*>(smem_raw);
   double* s_u = sm + S::u;
   double* s_A = sm + S::A;
   double* s_B = sm + S::B;
+  double* s_LQ = sm + S::LQ;
+  double* s_GQ = sm + S::GQ;
+  double* s_XB = sm + S::XB;
   __shared__ double v[15];
-  __shared__ double red[2][256];
+  __shared__ double red[2][NW];
   const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int x = tid; x < d::nrow * Q; x += nthr) s_LQ[x] = gtab[G.LQ + x];
+  for (int x = tid; x < d::n1 * Q; x += nthr) s_GQ[x] = gtab[G.GQ + x];
   double e2 = 0.0, n2 = 0.0;
   double ct, st;
   d_time_factors(bc, t, &ct, &st);
@@ -685,60 +715,80 @@ __global__ void __launch_bounds__(256)
     for (int x = tid; x < 4 * d::Np; x += nthr) s_u[x] = (double)q[e * 4 * d::Np + x];
     if (tid < 15) v[tid] = ev[e * 15 + tid];
     __syncthreads();
-    for (int x = tid; x < 4 * d::nrow * Q; x += nthr) {
-      const int p = x % Q;
-      const int tt = x / Q;
-      const int row = tt % d::nrow, f = tt / d::nrow;
-      int k, j;
-      decode_row(row, k, j);
+    for (int x = tid; x < Q * Q; x += nthr) {
+      const int p = x % Q, qq = x / Q;
+      double B[3], Ba[3], Bb[3], D[3], g1[3];
+      d_bilinear(v, gtab[G.XQ + p], gtab[G.XQ + qq], B, Ba, Bb);
+      for (int m = 0; m < 3; ++m) D[m] = 0.5 * (v[12 + m] - B[m]);
+      d_cross(Bb, D, g1);
+      s_XB[4 * x + 0] = B[0];
+      s_XB[4 * x + 1] = B[1];
+      s_XB[4 * x + 2] = B[2];
+      s_XB[4 * x + 3] = gtab[G.WQ + p] * gtab[G.WQ + qq] * (Ba[0] * g1[0] + Ba[1] * g1[1] + Ba[2] * g1[2]);
+    }
+    for (int x = tid; x < 4 * d::nrow * Q; x += nthr) {  // a pass, level-major
+      int k = 0;
+      while (x >= 4 * Q * tri_num(k + 1)) ++k;
+      const int rem = x - 4 * Q * tri_num(k);
+      const int f = rem / ((k + 1) * Q);
+      const int j = (rem / Q) % (k + 1);
+      const int p = rem % Q;
       const double* uc = s_u + f * d::Np + lvl_off(k) + j * (k + 1);
+      const double* lq = s_LQ + tri_num(k) * Q + p;
       double acc = 0;
-      for (int i = 0; i <= k; ++i) acc += uc[i] * gtab[G.LQ + (tri_num(k) + i) * Q + p];
-      s_A[x] = acc;
+      for (int i = 0; i <= k; ++i) acc += uc[i] * lq[i * Q];
+      s_A[(f * d::nrow + tri_num(k) + j) * Q + p] = acc;
     }
     __syncthreads();
-    for (int x = tid; x < 4 * d::n1 * Q * Q; x += nthr) {
+    for (int x = tid; x < 4 * d::n1 * Q * Q; x += nthr) {  // b pass, level-major
       const int pq = x % (Q * Q);
       const int tt = x / (Q * Q);
-      const int k = tt % d::n1, f = tt / d::n1;
+      const int f = tt % 4, k = tt / 4;
       const int p = pq % Q, qq = pq / Q;
+      const double* Ar = s_A + (f * d::nrow + tri_num(k)) * Q + p;
+      const double* lq = s_LQ + tri_num(k) * Q + qq;
       double acc = 0;
-      for (int j = 0; j <= k; ++j)
-        acc += s_A[(f * d::nrow + tri_num(k) + j) * Q + p] * gtab[G.LQ + (tri_num(k) + j) * Q + qq];
-      s_B[x] = acc;
+      for (int j = 0; j <= k; ++j) acc += Ar[j * Q] * lq[j * Q];
+      s_B[(f * d::n1 + k) * Q * Q + pq] = acc;
     }
     __syncthreads();
-    for (int x = tid; x < Q * Q * Q; x += nthr) {
+    for (int x = tid; x < Q * Q * Q; x += nthr) {  // c pass and the error integrand
       const int pq = x % (Q * Q), r = x / (Q * Q);
-      const int p = pq % Q, qq = pq / Q;
-      const double a = gtab[G.XQ + p], b = gtab[G.XQ + qq], c = gtab[G.XQC + r];
-      double B[3], Ba[3], Bb[3], X[3], Ue[4];
-      d_bilinear(v, a, b, B, Ba, Bb);
-      for (int m = 0; m < 3; ++m) X[m] = 0.5 * (1 - c) * B[m] + 0.5 * (1 + c) * v[12 + m];
-      const double w = gtab[G.WQ + p] * gtab[G.WQ + qq] * gtab[G.WQC + r] * d_jacobian(v, a, b);
-      d_exact(bc, X[0], X[1], X[2], ct, st, Ue);
+      const double c = gtab[G.XQC + r];
+      const double* xb = s_XB + 4 * pq;
+      double Ue[4];
+      d_exact(bc, 0.5 * (1 - c) * xb[0] + 0.5 * (1 + c) * v[12], 0.5 * (1 - c) * xb[1] + 0.5 * (1 + c) * v[13],
+              0.5 * (1 - c) * xb[2] + 0.5 * (1 + c) * v[14], ct, st, Ue);
+      const double w = xb[3] * gtab[G.WQC + r];
+#pragma unroll
       for (int f = 0; f < 4; ++f) {
         double uh = 0;
-        for (int k = 0; k <= N; ++k) uh += gtab[G.GQ + k * Q + r] * s_B[(f * d::n1 + k) * Q * Q + pq];
+#pragma unroll
+        for (int k = 0; k <= N; ++k) uh += s_GQ[k * Q + r] * s_B[(f * d::n1 + k) * Q * Q + pq];
         const double df = uh - Ue[f];
         e2 += w * df * df;
         n2 += w * Ue[f] * Ue[f];
       }
     }
   }
-  red[0][tid] = e2;
-  red[1][tid] = n2;
-  __syncthreads();
-  for (int s = nthr / 2; s > 0; s >>= 1) {
-    if (tid < s) {
-      red[0][tid] += red[0][tid + s];
-      red[1][tid] += red[1][tid + s];
-    }
-    __syncthreads();
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    e2 += __shfl_down_sync(0xffffffffu, e2, off);
+    n2 += __shfl_down_sync(0xffffffffu, n2, off);
   }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = e2;
+    red[1][tid >> 5] = n2;
+  }
+  __syncthreads();
   if (tid == 0) {
-    partial[2 * blockIdx.x] = red[0][0];
-    partial[2 * blockIdx.x + 1] = red[1][0];
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < NW; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    partial[2 * blockIdx.x] = a;
+    partial[2 * blockIdx.x + 1] = b;
   }
 }
 

@@ -13,7 +13,8 @@ struct Impl {
   static_assert(TraceSmem<N, T>::bytes <= kMaxSmem, "trace kernel shared memory");
   static_assert(RhsSmem<N, T>::bytes <= kMaxSmem, "rhs kernel shared memory");
   static_assert(ProjSmem<N>::bytes + 15 * 8 <= kMaxSmem, "projection kernel shared memory");
-  static_assert(ErrSmem<N>::bytes + 17 * 256 <= kMaxSmem, "error kernel shared memory");
+  static_assert(ErrSmem<N>::bytes + 8 * (15 + 2 * 16) <= kMaxSmem, "error kernel shared memory");
+  static_assert(4 * Dims<N>::n2 <= 4 * Dims<N>::n1 * Dims<N>::P3 * Dims<N>::P3, "projection B/J scratch");
 
   static cudaError_t prepare() {
     cudaError_t e = cudaFuncSetAttribute(trace_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -57,7 +58,7 @@ struct Impl {
   }
   static void error(int64_t K, const void* q, const double* ev, const double* gtab, int bc, double t,
                     double* partial, int nblocks, cudaStream_t s) {
-    error_kernel<N, T><<<nblocks, 256, ErrSmem<N>::bytes, s>>>(K, (const T*)q, ev, gtab, bc, t, partial);
+    error_kernel<N, T><<<nblocks, ErrCfg<N>::NT, ErrSmem<N>::bytes, s>>>(K, (const T*)q, ev, gtab, bc, t, partial);
   }
   static Launchers make() {
     Launchers l;
