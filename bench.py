@@ -226,10 +226,19 @@ def measure_form(binding, nx, delta, seed, n, precision, steps, warmup, dev):
     out = {"mesh": f"{nx}^3 hexes x 6, +-{delta}h (seed {seed})", "K": s.K, "N": n, "Np": s.Np,
            "precision": precision, "steps": steps, "ms_per_step": ms / steps,
            "dof_updates_per_s_per_stage": s.K * s.Np * 4 * 5 * steps / (ms * 1e-3),
-           "rhs_kernel_ms": prof["rhs"][0] / prof["rhs"][1], "trace_kernel_ms": prof["trace"][0] / prof["trace"][1],
+           "stage_kernel_ms": prof["rhs"][0] / prof["rhs"][1],
+           "trace_kernel_ms": prof["trace"][0] / prof["trace"][1] if prof["trace"][1] else 0.0,
+           "launches_per_step": (prof["rhs"][1] + prof["trace"][1]) / steps,
            "l2_rel_error_vs_exact": err_rel, "t_end": (warmup + steps) * dt}
     s.close()
     return out
+
+
+def workload_name(nx, n, prec):
+    if (nx, n, prec) == (NX, N, "f64"):
+        return WORKLOAD
+    return (f"unit cube, {nx}^3 hexes x 6 pyramids = {6 * nx ** 3}, +-0.05h vertex perturbation (seed 1), "
+            f"N={n} (Np={num_modes(n)}), 4 fields, upwind flux, rigid wall, standing wave, LSRK4 at CFL 0.5, {prec}")
 
 
 def main():
@@ -241,6 +250,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32 precision-form measurements")
     ap.add_argument("--nx", type=int, default=NX, help="hexes per axis (32 = the benchmark workload)")
+    ap.add_argument("--degree", type=int, default=N, help="polynomial degree (4 = the benchmark workload)")
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32"],
+                    help="f64 = the benchmark workload; f32 = the precision form (for profiling runs)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -259,8 +271,10 @@ def main():
     torch.cuda.set_device(dev)
     device = torch.device("cuda", dev)
     v, e = make_pyramid_mesh(args.nx, delta=DELTA, seed=SEED)
-    s = binding.Solver(v, e, N, precision="f64", bc="wall", tau=1.0, device=dev)
+    nd, prec = args.degree, args.precision
+    s = binding.Solver(v, e, nd, precision=prec, bc="wall", tau=1.0, device=dev)
     K, Np = s.K, s.Np
+    tb = 8 if prec == "f64" else 4
     dt = s.dt_cfl(0.5)
     s.project(0.0)
     stream = torch.cuda.current_stream(device)
@@ -292,18 +306,18 @@ def main():
     # ---- roofline of the dominant kernel (fused stage kernel), FP64 ALU bound
     rhs_ms, rhs_n = prof["rhs"]
     tr_ms, tr_n = prof["trace"]
-    peak = binding.fma_peak("f64")
+    peak = binding.fma_peak(prec)
     rhs_avg_s = rhs_ms / rhs_n * 1e-3
-    achieved = rhs_flops_per_element(N) * K / rhs_avg_s / 1e12
+    achieved = rhs_flops_per_element(nd) * K / rhs_avg_s / 1e12
     # DRAM bytes per element of the fused stage kernel, from the ncu capture summarised in
     # profiles/rhs_kernel_n4_f64_24cube.md (82,944 pyramids, N = 4, FP64: 1196.3 MB read +
     # write per launch); traffic scales with the element count. Valid for that kernel
     # version only: reset to None when the kernel changes, until it is measured again.
-    traffic = 14423.0 * K if (N == 4 and args.nx >= 24) else None
+    traffic = 14423.0 * K if (nd == 4 and prec == "f64" and args.nx >= 24) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "rhs_kernel<4,double,update>",
-                "peak_kind": "FP64 FMA throughput measured in this run (nominal 1.25)",
-                "kernel_ms_avg": rhs_ms / rhs_n, "trace_kernel_ms_avg": tr_ms / tr_n,
+                "traffic": traffic, "kernel": f"rhs_kernel<{nd},{'double' if prec == 'f64' else 'float'},update>",
+                "peak_kind": f"{prec.upper()} FMA throughput measured in this run",
+                "kernel_ms_avg": rhs_ms / rhs_n, "trace_kernel_ms_avg": tr_ms / tr_n if tr_n else 0.0,
                 "kernel_share": rhs_ms / (rhs_ms + tr_ms)}
 
     # ---- end to end through the public API with host buffers (state at t = 0 re-sent every step)
@@ -342,14 +356,15 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.nx == NX else WORKLOAD.replace("32^3", f"{args.nx}^3"), "K": K, "N": N, "Np": Np, "dt": dt, "step": "1 LSRK4 step = 5 RK stages",
-                   "l2_flush": f"inputs larger than L2 (state {K * Np * 32 / 1e6:.0f} MB, traces "
-                               f"{K * 5 * (N + 1) ** 2 * 32 / 1e6:.0f} MB per stage, 129 MB L2)",
+        "vs_baseline": None, "dtype": prec, "data": "synthetic",
+        "config": {"workload": workload_name(args.nx, nd, prec), "K": K, "N": nd, "Np": Np, "dt": dt,
+                   "step": "1 LSRK4 step = 5 RK stages",
+                   "l2_flush": f"inputs larger than L2 (state {K * Np * 4 * tb / 1e6:.0f} MB, traces "
+                               f"{K * 5 * (nd + 1) ** 2 * 4 * tb / 1e6:.0f} MB per stage, 129 MB L2)",
                    "parallelism": f"replicas x{world}"},
         "clocks": clocks.summary(),
         "e2e": e2e,
-        "gpu_launches": 2 * stages,
+        "gpu_launches": rhs_n + tr_n,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "l2_error_vs_exact": {"abs": err_abs, "rel": err_rel},

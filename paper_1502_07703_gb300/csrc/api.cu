@@ -60,6 +60,11 @@ struct pyr_dg {
        *tab = nullptr;
   double *tabd = nullptr, *gtab = nullptr, *ev = nullptr, *partial = nullptr;
   int32_t* mapP = nullptr;
+  // FP32 handles: second trace buffer; trbuf[tr_cur] holds the traces of q when tr_valid
+  void* tr2 = nullptr;
+  int tr_cur = 0;
+  bool tr_valid = false;
+  int stage_blocks = 0;
   // per-kernel event timing of pyr_dg_step (pyr_dg_profile)
   bool profiling = false;
   std::vector<cudaEvent_t> events;
@@ -130,7 +135,7 @@ void free_all(pyr_dg* h) {
   for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
   h->events.clear();
   void* ptrs[] = {h->q,    h->res,  h->tr, h->geo,     h->gface, h->invM, h->tab,
-                  h->tabd, h->gtab, h->ev, h->partial, h->mapP};
+                  h->tabd, h->gtab, h->ev, h->partial, h->mapP, h->tr2};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -262,8 +267,10 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
       {(void**)&h->ev, (size_t)K * 15 * 8},
       {(void**)&h->partial, (size_t)h->err_blocks * 2 * 8},
       {(void**)&h->mapP, (size_t)K * Nfc * 4},
+      {&h->tr2, h->L->stage32 ? (size_t)K * Nfc * 4 * ts : 0},
   };
   for (auto& a : allocs) {
+    if (a.bytes == 0) continue;
     cudaError_t e = cudaMalloc(a.p, a.bytes);
     if (e != cudaSuccess) {
       free_all(h);
@@ -281,6 +288,10 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   cudaError_t e = cudaSuccess;
   cudaStream_t s = h->stream;
   if (e == cudaSuccess) e = h->L->prepare();
+  if (e == cudaSuccess && h->L->upload_c32) {
+    e = h->L->upload_c32(T.tab.data());
+    h->stage_blocks = (int)std::min<int64_t>(K, (int64_t)(nsm > 0 ? nsm : 1) * h->L->blocks_per_sm32());
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->tab, tabsrc, (size_t)TL.size * ts, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->tabd, T.tab.data(), (size_t)TL.size * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->gtab, T.geo.data(), (size_t)G.size * 8, cudaMemcpyHostToDevice, s);
@@ -321,6 +332,7 @@ int pyr_dg_project(pyr_dg* h, double t0) {
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemsetAsync(h->res, 0, (size_t)h->K * 4 * h->Np * h->tsize, h->stream));
   h->t = t0;
+  h->tr_valid = false;
   return PYR_DG_OK;
 }
 
@@ -335,6 +347,7 @@ int pyr_dg_set_state(pyr_dg* h, const void* q, int where, double t) {
   CUDA_TRY(cudaMemsetAsync(h->res, 0, bytes, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   h->t = t;
+  h->tr_valid = false;
   return PYR_DG_OK;
 }
 
@@ -358,6 +371,7 @@ int pyr_dg_rhs(pyr_dg* h, const void* q_dev, void* rhs_dev) {
   h->L->trace(h->K, q_dev, h->tab, h->tr, h->stream);
   h->L->rhs_out(h->K, q_dev, rhs_dev, h->tr, h->mapP, h->geo, h->gface, h->invM, h->tab, h->bc, h->tau, h->stream);
   CUDA_TRY(cudaGetLastError());
+  h->tr_valid = false;  // the trace buffer was used as scratch
   return PYR_DG_OK;
 }
 
@@ -366,6 +380,29 @@ int pyr_dg_step(pyr_dg* h, int nsteps, double dt) {
   if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(PYR_DG_ERR_BAD_ARG, "need nsteps >= 0, dt > 0");
   DeviceGuard g(h->device);
   CUDA_TRY(g.err);
+  if (h->L->stage32 && nsteps > 0) {
+    // FP32: one launch per stage; traces ping-pong between tr and tr2
+    void* buf[2] = {h->tr, h->tr2};
+    size_t slot = 0;
+    if (!h->tr_valid) {
+      CUDA_TRY(prof_begin(h, 0, &slot));
+      h->L->trace(h->K, h->q, h->tab, buf[h->tr_cur], h->stream);
+      CUDA_TRY(prof_end(h, slot));
+    }
+    for (int n = 0; n < nsteps; ++n) {
+      for (int s = 0; s < 5; ++s) {
+        CUDA_TRY(prof_begin(h, 1, &slot));
+        h->L->stage32(h->K, h->q, h->res, buf[h->tr_cur], buf[1 - h->tr_cur], h->mapP, h->geo, h->gface, h->invM,
+                      h->bc, h->tau, kRkA[s], kRkB[s], dt, 1, h->stage_blocks, h->stream);
+        CUDA_TRY(prof_end(h, slot));
+        h->tr_cur = 1 - h->tr_cur;
+      }
+    }
+    CUDA_TRY(cudaGetLastError());
+    h->tr_valid = true;
+    h->t += nsteps * dt;
+    return PYR_DG_OK;
+  }
   for (int n = 0; n < nsteps; ++n) {
     for (int s = 0; s < 5; ++s) {
       size_t slot = 0;

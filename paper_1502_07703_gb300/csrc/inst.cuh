@@ -1,6 +1,7 @@
 // Instantiation of the stage kernels for one degree; included by inst_n<N>.cu.
 #pragma once
 #include "dg_kernels.cuh"
+#include "stage32.cuh"
 #include "launch.h"
 
 namespace pyrdg {
@@ -15,6 +16,7 @@ struct Impl {
   static_assert(ProjSmem<N>::bytes + 15 * 8 <= kMaxSmem, "projection kernel shared memory");
   static_assert(ErrSmem<N>::bytes + 8 * (15 + 2 * 16) <= kMaxSmem, "error kernel shared memory");
   static_assert(4 * Dims<N>::n2 <= 4 * Dims<N>::n1 * Dims<N>::P3 * Dims<N>::P3, "projection B/J scratch");
+  static_assert(S32<N>::bytes <= kMaxSmem, "FP32 stage kernel shared memory");
 
   static cudaError_t prepare() {
     cudaError_t e = cudaFuncSetAttribute(trace_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -60,6 +62,47 @@ struct Impl {
                     double* partial, int nblocks, cudaStream_t s) {
     error_kernel<N, T><<<nblocks, ErrCfg<N>::NT, ErrSmem<N>::bytes, s>>>(K, (const T*)q, ev, gtab, bc, t, partial);
   }
+  static void stage32(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
+                      const void* geo, const void* gface, const void* invM, int bc, double tau, double rka, double rkb,
+                      double dt, int write_traces, int nblocks, cudaStream_t s) {
+    stage32_kernel<N><<<nblocks, S32<N>::NT, S32<N>::bytes, s>>>(
+        K, (float*)q, (float*)res, (const float*)tr_cur, (float*)tr_nxt, mapP, (const float*)geo,
+        (const float*)gface, (const float*)invM, bc, (float)tau, (float)rka, (float)rkb, (float)dt, write_traces);
+  }
+  static cudaError_t upload_c32(const double* tab) {
+    using C = C32<N>;
+    constexpr TabLayout L(N);
+    static_assert(C::size <= C32<7>::size, "constant table size");
+    float h[C::size];
+    for (int x = 0; x < d::nrow * d::P3; ++x) h[C::LX + x] = (float)tab[L.LX + x];
+    for (int x = 0; x < d::nrow * d::n1; ++x) h[C::DL + x] = (float)tab[L.DL + x];
+    for (int x = 0; x < d::n2; ++x) {
+      h[C::MH + x] = (float)tab[L.MH + x];
+      h[C::MG + x] = (float)tab[L.MG + x];
+      h[C::GF + x] = (float)tab[L.GF + x];
+      h[C::WB + x] = (float)tab[L.WB + x];
+      h[C::WFT + x] = (float)tab[L.WFT + x];
+    }
+    for (int k = 0; k <= N; ++k) h[C::GB + k] = (float)tab[L.GB + k];
+    for (int k = 0; k <= N; ++k)
+      for (int j = 0; j <= k; ++j) {
+        const int r = tri_num(k) + j;
+        for (int c = 0; c <= N; ++c) {
+          h[C::CB + r * d::n1 + c] = (float)(tab[L.GB + k] * tab[L.LX + r * d::P3 + c]);
+          h[C::CFm + r * d::n1 + c] = (float)(tab[L.GF + k * d::n1 + c] * tab[L.LX + r * d::P3 + d::n1]);
+          h[C::CFp + r * d::n1 + c] = (float)(tab[L.GF + k * d::n1 + c] * tab[L.LX + r * d::P3 + d::n1 + 1]);
+        }
+      }
+    cudaError_t e = cudaMemcpyToSymbol(c32, h, sizeof(float) * C::size);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(stage32_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S32<N>::bytes);
+  }
+  static int blocks_per_sm32() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage32_kernel<N>, S32<N>::NT, S32<N>::bytes) != cudaSuccess)
+      return 1;
+    return n > 0 ? n : 1;
+  }
   static Launchers make() {
     Launchers l;
     l.nt = NT;
@@ -74,6 +117,17 @@ struct Impl {
     l.rhs_out = &rhs_out;
     l.project = &project;
     l.error = &error;
+    if (sizeof(T) == 4) {
+      l.stage32 = &stage32;
+      l.upload_c32 = &upload_c32;
+      l.blocks_per_sm32 = &blocks_per_sm32;
+      l.smem_stage32 = S32<N>::bytes;
+    } else {
+      l.stage32 = nullptr;
+      l.upload_c32 = nullptr;
+      l.blocks_per_sm32 = nullptr;
+      l.smem_stage32 = 0;
+    }
     return l;
   }
 };

@@ -22,6 +22,17 @@ struct Launchers {
                   cudaStream_t s);
   void (*error)(int64_t K, const void* q, const double* ev, const double* gtab, int bc, double t, double* partial,
                 int nblocks, cudaStream_t s);
+  // Single-launch FP32 stage (null for double): reads traces of q from tr_cur, writes
+  // the updated state, residual and (if write_traces) the new traces into tr_nxt.
+  void (*stage32)(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
+                  const void* geo, const void* gface, const void* invM, int bc, double tau, double rka, double rkb,
+                  double dt, int write_traces, int nblocks, cudaStream_t s);
+  // Fill the FP32 stage kernel's constant tables on the current device from the
+  // double reference tables (TabLayout); null for double.
+  cudaError_t (*upload_c32)(const double* tab);
+  // Resident CTAs per SM of the FP32 stage kernel (for its persistent grid); 0 for double.
+  int (*blocks_per_sm32)();
+  size_t smem_stage32;
 };
 
 // precision: 0 = double, 1 = float. Returns null for an unsupported degree.

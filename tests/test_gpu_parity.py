@@ -119,6 +119,48 @@ def test_f32_evolution_matches_oracle(torch_cuda):
     assert rel <= TOL["f32"], rel
 
 
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 6, 7])
+def test_f32_stage_kernel_all_degrees(torch_cuda, N):
+    """The single-launch FP32 stage kernel (ping-pong traces) at every degree:
+    5 steps taken one call at a time, against the oracle."""
+    v, e = make_pyramid_mesh(2, 2, 1, delta=0.1, seed=40 + N)
+    dg = PyramidDG(v, e, N)
+    dt = dg.dt_cfl(0.5)
+    U_or = dg.lsrk4(dg.project_exact(0.0), dt, 5)
+    with _solver(v, e, N, precision="f32") as s:
+        s.project(0.0)
+        for _ in range(5):
+            s.step(1, dt)
+        Ug = s.get_state().astype(np.float64)
+    rel = dg.rel_l2_points(dg.values_phi(Ug), dg.values_psi(U_or))
+    assert rel <= TOL["f32"], rel
+
+
+@pytest.mark.parametrize("bc,tau", [("wall", 0.0), ("free", 1.0)])
+def test_f32_stage_kernel_invalidation_and_variants(torch_cuda, bc, tau):
+    """Traces stay consistent when stepping is interleaved with rhs (which uses the
+    trace buffer as scratch) and with set_state (which replaces the state)."""
+    torch = torch_cuda
+    v, e = make_pyramid_mesh(2, 2, 2, delta=0.08, seed=9, domain=_domain(bc))
+    N = 3
+    dg = PyramidDG(v, e, N, tau=tau, bc=bc)
+    dt = dg.dt_cfl(0.5)
+    U0 = random_state(dg.K, dg.Np, 77).astype(np.float32)
+    U_or = dg.lsrk4(dg.psi_from_phi(U0.astype(np.float64)), dt, 4)
+    with _solver(v, e, N, precision="f32", bc=bc, tau=tau) as s:
+        s.project(0.0)
+        s.step(2, dt)                      # traces of the projected state become valid
+        s.set_state(U0)                    # must invalidate them
+        s.step(1, dt)
+        s.rhs(torch.zeros(s.shape, dtype=s.torch_dtype, device="cuda"))  # scratch use of the trace buffer
+        s.step(1, dt)
+        s.step(2, dt)
+        Ug = s.get_state().astype(np.float64)
+    # set_state zeroes the residual, so the reference restarts the 2N-storage scheme too
+    rel = dg.rel_l2_points(dg.values_phi(Ug), dg.values_psi(U_or))
+    assert rel <= TOL["f32"], rel
+
+
 def test_state_roundtrip_host_and_device(torch_cuda):
     torch = torch_cuda
     v, e = make_pyramid_mesh(2, 1, 1, delta=0.1, seed=3)
