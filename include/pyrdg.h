@@ -180,6 +180,44 @@ void pyr_dg_destroy(pyr_dg* h);
 /* Message for the last failing call on this thread ("" if none). */
 const char* pyr_dg_last_error(void);
 
+/* ---- batched form: many independent meshes of uneven sizes and degrees ----
+ * The meshes of one degree are held as one disjoint-union mesh, so every RK
+ * stage is one persistent launch per distinct degree over all of its meshes,
+ * with each element using its own mesh's time step; one pyr_dg_batch_step
+ * call is a captured CUDA graph (captured on first use for a given nsteps,
+ * replayed afterwards). For PYR_DG_F32 batches the persistent grid of each
+ * degree is autotuned at setup (timed on the all-zero initial state). The
+ * state, time and errors are per mesh. opts applies to every mesh; with
+ * opts->stream NULL the batch creates its own non-blocking stream (graph
+ * capture needs one), reported by pyr_dg_batch_stream. */
+typedef struct pyr_dg_batch pyr_dg_batch;
+
+/* vertices[i] (Nv[i] x 3 doubles), EToV[i] (K[i] x 5 int32) and N[i] describe
+ * mesh i, i < nmesh; all host arrays, copied. Errors as pyr_dg_setup. */
+int pyr_dg_batch_setup(int nmesh, const double* const* vertices, const int64_t* Nv, const int32_t* const* EToV,
+                       const int64_t* K, const int* N, const pyr_dg_opts* opts, pyr_dg_batch** out);
+/* Number of meshes, of degree groups (= launches per stage), total elements and
+ * total degrees of freedom (sum of K * 4 * Np). Any pointer may be NULL. */
+int pyr_dg_batch_info(const pyr_dg_batch* b, int* nmesh, int* ngroups, int64_t* total_K, int64_t* total_dofs);
+/* Degree, element count and launch grid (the autotuned persistent grid for FP32)
+ * of degree group `group` < ngroups. */
+int pyr_dg_batch_group_info(const pyr_dg_batch* b, int group, int* N, int64_t* K, int* stage_blocks);
+/* Project the exact standing wave at t0 into every mesh; sets every mesh's time to t0. */
+int pyr_dg_batch_project(pyr_dg_batch* b, double t0);
+/* Per-mesh CFL time steps (as pyr_dg_dt_cfl) into dt[nmesh]. */
+int pyr_dg_batch_dt_cfl(const pyr_dg_batch* b, double cfl, double* dt);
+/* Advance every mesh nsteps LSRK4 steps of its own dt[i] > 0. Asynchronous. */
+int pyr_dg_batch_step(pyr_dg_batch* b, int nsteps, const double* dt);
+/* Per-mesh L2 errors (as pyr_dg_error) into l2_abs[nmesh], l2_rel[nmesh]
+ * (either may be NULL). Synchronises. */
+int pyr_dg_batch_error(pyr_dg_batch* b, double* l2_abs, double* l2_rel);
+/* Copy the state of mesh `mesh` (K[mesh] x 4 x Np elements) to q on the host or
+ * device (`where`). Synchronises. */
+int pyr_dg_batch_get_state(pyr_dg_batch* b, int mesh, void* q, int where);
+int pyr_dg_batch_sync(pyr_dg_batch* b);
+void* pyr_dg_batch_stream(const pyr_dg_batch* b);
+void pyr_dg_batch_destroy(pyr_dg_batch* b);
+
 /* ---- host-side builder queries (no GPU needed; used to test the builder) ---- */
 
 /* n-point Gauss-Jacobi rule for weight (1-x)^alpha (1+x)^beta on [-1,1]

@@ -68,6 +68,18 @@ _SIGNATURES = {
     "pyr_dg_fma_peak": (ctypes.c_int, [ctypes.c_int, _c_dp]),
     "pyr_dg_rhs_noalloc": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_void_p]),
     "pyr_dg_profile": (ctypes.c_int, [_c_h, ctypes.c_int]),
+    "pyr_dg_batch_setup": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_c_dp), _c_i64p, ctypes.POINTER(_c_i32p),
+                                          _c_i64p, _c_ip, ctypes.POINTER(Opts), ctypes.POINTER(_c_h)]),
+    "pyr_dg_batch_info": (ctypes.c_int, [_c_h, _c_ip, _c_ip, _c_i64p, _c_i64p]),
+    "pyr_dg_batch_group_info": (ctypes.c_int, [_c_h, ctypes.c_int, _c_ip, _c_i64p, _c_ip]),
+    "pyr_dg_batch_project": (ctypes.c_int, [_c_h, ctypes.c_double]),
+    "pyr_dg_batch_dt_cfl": (ctypes.c_int, [_c_h, ctypes.c_double, _c_dp]),
+    "pyr_dg_batch_step": (ctypes.c_int, [_c_h, ctypes.c_int, _c_dp]),
+    "pyr_dg_batch_error": (ctypes.c_int, [_c_h, _c_dp, _c_dp]),
+    "pyr_dg_batch_get_state": (ctypes.c_int, [_c_h, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+    "pyr_dg_batch_sync": (ctypes.c_int, [_c_h]),
+    "pyr_dg_batch_stream": (ctypes.c_void_p, [_c_h]),
+    "pyr_dg_batch_destroy": (None, [_c_h]),
     "pyr_dg_profile_read": (ctypes.c_int, [_c_h, _c_dp, _c_i64p, _c_dp, _c_i64p]),
 }
 
@@ -260,3 +272,96 @@ class Solver:
     def _require_device(self, t):
         if not (hasattr(t, "is_cuda") and t.is_cuda) or t.dtype != self.torch_dtype or tuple(t.shape) != self.shape:
             raise ValueError(f"expected a CUDA tensor of shape {self.shape} and dtype {self.torch_dtype}")
+
+
+class Batch:
+    """Many independent meshes advanced together (include/pyrdg.h, batched form).
+
+    meshes: list of (vertices (Nv, 3), EToV (K, 5), N). States are per mesh."""
+
+    def __init__(self, meshes, precision="f32", bc="wall", tau=1.0, device=None):
+        import torch
+
+        self._torch = torch
+        self._keep = [(np.ascontiguousarray(v, dtype=np.float64), np.ascontiguousarray(e, dtype=np.int32), int(n))
+                      for v, e, n in meshes]
+        nm = len(self._keep)
+        V = (_c_dp * nm)(*[_ptr(v, ctypes.c_double) for v, _, _ in self._keep])
+        E = (_c_i32p * nm)(*[_ptr(e, ctypes.c_int32) for _, e, _ in self._keep])
+        Nv = np.array([v.shape[0] for v, _, _ in self._keep], dtype=np.int64)
+        K = np.array([e.shape[0] for _, e, _ in self._keep], dtype=np.int64)
+        Ns = np.array([n for _, _, n in self._keep], dtype=np.int32)
+        o = Opts()
+        lib().pyr_dg_default_opts(ctypes.byref(o))
+        o.precision = {"f64": PYR_DG_F64, "f32": PYR_DG_F32}[precision]
+        o.bc = {"wall": PYR_DG_BC_WALL, "free": PYR_DG_BC_FREE}[bc]
+        o.tau = float(tau)
+        o.device = int(torch.cuda.current_device() if device is None else device)
+        o.stream = None
+        h = _c_h()
+        _check(lib().pyr_dg_batch_setup(nm, V, _ptr(Nv, ctypes.c_int64), E, _ptr(K, ctypes.c_int64),
+                                        _ptr(Ns, ctypes.c_int), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.nmesh = nm
+        self.K = K
+        self.N = Ns
+        self.Np = np.array([(n + 1) * (n + 2) * (2 * n + 3) // 6 for n in Ns])
+        self.np_dtype = np.float64 if precision == "f64" else np.float32
+        nmesh, ng, tk, td = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().pyr_dg_batch_info(h, ctypes.byref(nmesh), ctypes.byref(ng), ctypes.byref(tk), ctypes.byref(td)))
+        self.ngroups, self.total_K, self.total_dofs = ng.value, tk.value, td.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pyr_dg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def groups(self):
+        out = []
+        for g in range(self.ngroups):
+            n, k, b = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
+            _check(lib().pyr_dg_batch_group_info(self._h, g, ctypes.byref(n), ctypes.byref(k), ctypes.byref(b)))
+            out.append({"N": n.value, "K": k.value, "stage_blocks": b.value})
+        return out
+
+    @property
+    def stream_ptr(self):
+        return lib().pyr_dg_batch_stream(self._h)
+
+    def project(self, t0=0.0):
+        _check(lib().pyr_dg_batch_project(self._h, float(t0)))
+
+    def dt_cfl(self, cfl=0.5):
+        dt = np.empty(self.nmesh)
+        _check(lib().pyr_dg_batch_dt_cfl(self._h, float(cfl), _ptr(dt, ctypes.c_double)))
+        return dt
+
+    def step(self, nsteps, dt):
+        dt = np.ascontiguousarray(dt, dtype=np.float64)
+        _check(lib().pyr_dg_batch_step(self._h, int(nsteps), _ptr(dt, ctypes.c_double)))
+
+    def error(self):
+        a = np.empty(self.nmesh)
+        r = np.empty(self.nmesh)
+        _check(lib().pyr_dg_batch_error(self._h, _ptr(a, ctypes.c_double), _ptr(r, ctypes.c_double)))
+        return a, r
+
+    def get_state(self, mesh):
+        out = np.empty((int(self.K[mesh]), 4, int(self.Np[mesh])), dtype=self.np_dtype)
+        _check(lib().pyr_dg_batch_get_state(self._h, int(mesh), out.ctypes.data, PYR_DG_HOST))
+        return out
+
+    def sync(self):
+        _check(lib().pyr_dg_batch_sync(self._h))

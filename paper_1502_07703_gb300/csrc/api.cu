@@ -13,6 +13,7 @@
 
 #include "../../include/pyrdg.h"
 #include "builder.h"
+#include "handle.h"
 #include "launch.h"
 
 namespace pyrdg {
@@ -39,42 +40,16 @@ const Launchers* get_launchers(int N, int precision) {
 }  // namespace pyrdg
 
 // Carpenter & Kennedy (1994) 5-stage 2N-storage RK4 (cited in Sec. 4.1).
-static const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
-                               -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
-static const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
-                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
-                               2277821191437.0 / 14882151754819.0};
-
-struct pyr_dg {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int N = 0, Np = 0, Nfc = 0, precision = 0, bc = 0;
-  double tau = 1.0;
-  int64_t K = 0;
-  size_t tsize = 8;
-  double t = 0.0;
-  double max_aov = 0.0;
-  int err_blocks = 0;
-  const pyrdg::Launchers* L = nullptr;
-  void *q = nullptr, *res = nullptr, *tr = nullptr, *geo = nullptr, *gface = nullptr, *invM = nullptr,
-       *tab = nullptr;
-  double *tabd = nullptr, *gtab = nullptr, *ev = nullptr, *partial = nullptr;
-  int32_t* mapP = nullptr;
-  // FP32 handles: second trace buffer; trbuf[tr_cur] holds the traces of q when tr_valid
-  void* tr2 = nullptr;
-  int tr_cur = 0;
-  bool tr_valid = false;
-  int stage_blocks = 0;
-  // per-kernel event timing of pyr_dg_step (pyr_dg_profile)
-  bool profiling = false;
-  std::vector<cudaEvent_t> events;
-  std::vector<int> event_kind;  // per recorded pair: 0 trace, 1 rhs
-  size_t events_used = 0;
-};
+const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                        -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                        1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                        2277821191437.0 / 14882151754819.0};
 
 static thread_local std::string g_err;
 
-static int fail(int code, const char* fmt, ...) {
+namespace pyrdg {
+int fail(int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -83,32 +58,12 @@ static int fail(int code, const char* fmt, ...) {
   g_err = buf;
   return code;
 }
+}  // namespace pyrdg
 
-#define CUDA_TRY(expr)                                                                    \
-  do {                                                                                    \
-    cudaError_t _e = (expr);                                                              \
-    if (_e != cudaSuccess)                                                                \
-      return fail(PYR_DG_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(_e));      \
-  } while (0)
+using pyrdg::DeviceGuard;
+using pyrdg::fail;
 
 namespace {
-// Makes the handle's device current for the duration of a call, restoring the caller's.
-struct DeviceGuard {
-  int prev = -1;
-  cudaError_t err = cudaSuccess;
-  explicit DeviceGuard(int dev) {
-    int cur = 0;
-    err = cudaGetDevice(&cur);
-    if (err == cudaSuccess && cur != dev) {
-      err = cudaSetDevice(dev);
-      if (err == cudaSuccess) prev = cur;
-    }
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
 // Record an event pair slot around the next launch when profiling (kind 0 trace, 1 rhs).
 cudaError_t prof_begin(pyr_dg* h, int kind, size_t* slot) {
   if (!h->profiling) return cudaSuccess;
@@ -135,11 +90,52 @@ void free_all(pyr_dg* h) {
   for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
   h->events.clear();
   void* ptrs[] = {h->q,    h->res,  h->tr, h->geo,     h->gface, h->invM, h->tab,
-                  h->tabd, h->gtab, h->ev, h->partial, h->mapP, h->tr2};
+                  h->tabd, h->gtab, h->ev, h->partial, h->mapP, h->tr2, h->dt_elem};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
 }  // namespace
+
+namespace pyrdg {
+int enqueue_steps(pyr_dg* h, int nsteps, double dt) {
+  if (h->L->stage32 && nsteps > 0) {
+    // FP32: one launch per stage; traces ping-pong between tr and tr2
+    void* buf[2] = {h->tr, h->tr2};
+    size_t slot = 0;
+    if (!h->tr_valid) {
+      CUDA_TRY(prof_begin(h, 0, &slot));
+      h->L->trace(h->K, h->q, h->tab, buf[h->tr_cur], h->stream);
+      CUDA_TRY(prof_end(h, slot));
+    }
+    for (int n = 0; n < nsteps; ++n) {
+      for (int s = 0; s < 5; ++s) {
+        CUDA_TRY(prof_begin(h, 1, &slot));
+        h->L->stage32(h->K, h->q, h->res, buf[h->tr_cur], buf[1 - h->tr_cur], h->mapP, h->geo, h->gface, h->invM,
+                      h->bc, h->tau, kRkA[s], kRkB[s], dt, h->dt_elem, 1, h->stage_blocks, h->stream);
+        CUDA_TRY(prof_end(h, slot));
+        h->tr_cur = 1 - h->tr_cur;
+      }
+    }
+    CUDA_TRY(cudaGetLastError());
+    h->tr_valid = true;
+    return PYR_DG_OK;
+  }
+  for (int n = 0; n < nsteps; ++n) {
+    for (int s = 0; s < 5; ++s) {
+      size_t slot = 0;
+      CUDA_TRY(prof_begin(h, 0, &slot));
+      h->L->trace(h->K, h->q, h->tab, h->tr, h->stream);
+      CUDA_TRY(prof_end(h, slot));
+      CUDA_TRY(prof_begin(h, 1, &slot));
+      h->L->rhs_update(h->K, h->q, h->res, h->tr, h->mapP, h->geo, h->gface, h->invM, h->tab, h->bc, h->tau, kRkA[s],
+                       kRkB[s], dt, h->dt_elem, h->stream);
+      CUDA_TRY(prof_end(h, slot));
+    }
+  }
+  CUDA_TRY(cudaGetLastError());
+  return PYR_DG_OK;
+}
+}  // namespace pyrdg
 
 extern "C" {
 
@@ -380,42 +376,8 @@ int pyr_dg_step(pyr_dg* h, int nsteps, double dt) {
   if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(PYR_DG_ERR_BAD_ARG, "need nsteps >= 0, dt > 0");
   DeviceGuard g(h->device);
   CUDA_TRY(g.err);
-  if (h->L->stage32 && nsteps > 0) {
-    // FP32: one launch per stage; traces ping-pong between tr and tr2
-    void* buf[2] = {h->tr, h->tr2};
-    size_t slot = 0;
-    if (!h->tr_valid) {
-      CUDA_TRY(prof_begin(h, 0, &slot));
-      h->L->trace(h->K, h->q, h->tab, buf[h->tr_cur], h->stream);
-      CUDA_TRY(prof_end(h, slot));
-    }
-    for (int n = 0; n < nsteps; ++n) {
-      for (int s = 0; s < 5; ++s) {
-        CUDA_TRY(prof_begin(h, 1, &slot));
-        h->L->stage32(h->K, h->q, h->res, buf[h->tr_cur], buf[1 - h->tr_cur], h->mapP, h->geo, h->gface, h->invM,
-                      h->bc, h->tau, kRkA[s], kRkB[s], dt, 1, h->stage_blocks, h->stream);
-        CUDA_TRY(prof_end(h, slot));
-        h->tr_cur = 1 - h->tr_cur;
-      }
-    }
-    CUDA_TRY(cudaGetLastError());
-    h->tr_valid = true;
-    h->t += nsteps * dt;
-    return PYR_DG_OK;
-  }
-  for (int n = 0; n < nsteps; ++n) {
-    for (int s = 0; s < 5; ++s) {
-      size_t slot = 0;
-      CUDA_TRY(prof_begin(h, 0, &slot));
-      h->L->trace(h->K, h->q, h->tab, h->tr, h->stream);
-      CUDA_TRY(prof_end(h, slot));
-      CUDA_TRY(prof_begin(h, 1, &slot));
-      h->L->rhs_update(h->K, h->q, h->res, h->tr, h->mapP, h->geo, h->gface, h->invM, h->tab, h->bc, h->tau, kRkA[s],
-                       kRkB[s], dt, h->stream);
-      CUDA_TRY(prof_end(h, slot));
-    }
-  }
-  CUDA_TRY(cudaGetLastError());
+  const int rc = pyrdg::enqueue_steps(h, nsteps, dt);
+  if (rc != PYR_DG_OK) return rc;
   h->t += nsteps * dt;
   return PYR_DG_OK;
 }

@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
     rhs_kernel(int64_t K, const T* qin, T* qout, T* __restrict__ res,  // qin == qout when updating in place
                const T* __restrict__ tr, const int32_t* __restrict__ mapP, const T* __restrict__ geo,
                const T* __restrict__ gface, const T* __restrict__ invM, const T* __restrict__ tab, int bc, T tau,
-               T rka, T rkb, T dt) {
+               T rka, T rkb, T dt, const T* __restrict__ dt_elem) {
   using d = Dims<N>;
   using S = RhsSmem<N, T>;
   constexpr TabLayout L(N);
@@ -576,7 +576,8 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
     const T rhs = -invM[e * d::Np + n] * acc;
     const int64_t gi = e * 4 * d::Np + x;
     if (UPDATE) {
-      const T rnew = rka * res[gi] + dt * rhs;
+      const T dte = dt_elem ? dt_elem[e] : dt;  // per-element step when meshes are batched
+      const T rnew = rka * res[gi] + dte * rhs;
       res[gi] = rnew;
       qout[gi] = s_u[x] + rkb * rnew;
     } else {

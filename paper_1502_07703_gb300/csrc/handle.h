@@ -1,0 +1,80 @@
+// Internal definition of the pyr_dg handle and helpers shared by the C-ABI
+// translation units (api.cu, batch.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pyrdg.h"
+#include "launch.h"
+
+// Carpenter & Kennedy (1994) 5-stage 2N-storage RK4 (cited in Sec. 4.1).
+extern const double kRkA[5];
+extern const double kRkB[5];
+
+struct pyr_dg {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int N = 0, Np = 0, Nfc = 0, precision = 0, bc = 0;
+  double tau = 1.0;
+  int64_t K = 0;
+  size_t tsize = 8;
+  double t = 0.0;
+  double max_aov = 0.0;
+  int err_blocks = 0;
+  const pyrdg::Launchers* L = nullptr;
+  void *q = nullptr, *res = nullptr, *tr = nullptr, *geo = nullptr, *gface = nullptr, *invM = nullptr,
+       *tab = nullptr;
+  double *tabd = nullptr, *gtab = nullptr, *ev = nullptr, *partial = nullptr;
+  int32_t* mapP = nullptr;
+  // FP32 handles: second trace buffer; trbuf[tr_cur] holds the traces of q when tr_valid
+  void* tr2 = nullptr;
+  int tr_cur = 0;
+  bool tr_valid = false;
+  int stage_blocks = 0;
+  // per-element time step (device, K elements of the handle's type) when the handle
+  // holds several batched meshes; null for a single mesh
+  void* dt_elem = nullptr;
+  // per-kernel event timing of pyr_dg_step (pyr_dg_profile)
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  std::vector<int> event_kind;  // per recorded pair: 0 trace, 1 rhs
+  size_t events_used = 0;
+};
+
+namespace pyrdg {
+
+// Set the thread-local message returned by pyr_dg_last_error and return code.
+int fail(int code, const char* fmt, ...);
+
+// Makes a device current for the duration of a call, restoring the caller's.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    int cur = 0;
+    err = cudaGetDevice(&cur);
+    if (err == cudaSuccess && cur != dev) {
+      err = cudaSetDevice(dev);
+      if (err == cudaSuccess) prev = cur;
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// Enqueue nsteps LSRK4 steps of the handle's state (the body of pyr_dg_step); with
+// dt_elem set on the handle each element uses its own step. Host-side bookkeeping of
+// the time is left to the caller.
+int enqueue_steps(pyr_dg* h, int nsteps, double dt);
+
+}  // namespace pyrdg
+
+#define CUDA_TRY(expr)                                                                          \
+  do {                                                                                          \
+    cudaError_t _e = (expr);                                                                    \
+    if (_e != cudaSuccess)                                                                      \
+      return pyrdg::fail(PYR_DG_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(_e));      \
+  } while (0)

@@ -43,16 +43,16 @@ struct Impl {
   }
   static void rhs_update(int64_t K, void* q, void* res, const void* tr, const int32_t* mapP, const void* geo,
                          const void* gface, const void* invM, const void* tab, int bc, double tau, double rka,
-                         double rkb, double dt, cudaStream_t s) {
+                         double rkb, double dt, const void* dt_elem, cudaStream_t s) {
     rhs_kernel<N, T, true><<<(unsigned)K, NT, RhsSmem<N, T>::bytes, s>>>(
         K, (const T*)q, (T*)q, (T*)res, (const T*)tr, mapP, (const T*)geo, (const T*)gface, (const T*)invM,
-        (const T*)tab, bc, (T)tau, (T)rka, (T)rkb, (T)dt);
+        (const T*)tab, bc, (T)tau, (T)rka, (T)rkb, (T)dt, (const T*)dt_elem);
   }
   static void rhs_out(int64_t K, const void* q, void* rhs, const void* tr, const int32_t* mapP, const void* geo,
                       const void* gface, const void* invM, const void* tab, int bc, double tau, cudaStream_t s) {
     rhs_kernel<N, T, false><<<(unsigned)K, NT, RhsSmem<N, T>::bytes, s>>>(
         K, (const T*)q, (T*)rhs, nullptr, (const T*)tr, mapP, (const T*)geo, (const T*)gface, (const T*)invM,
-        (const T*)tab, bc, (T)tau, (T)0, (T)0, (T)0);
+        (const T*)tab, bc, (T)tau, (T)0, (T)0, (T)0, nullptr);
   }
   static void project(int64_t K, const double* ev, const double* gtab, const double* tabd, int bc, double t, void* q,
                       cudaStream_t s) {
@@ -64,10 +64,11 @@ struct Impl {
   }
   static void stage32(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
                       const void* geo, const void* gface, const void* invM, int bc, double tau, double rka, double rkb,
-                      double dt, int write_traces, int nblocks, cudaStream_t s) {
+                      double dt, const void* dt_elem, int write_traces, int nblocks, cudaStream_t s) {
     stage32_kernel<N><<<nblocks, S32<N>::NT, S32<N>::bytes, s>>>(
         K, (float*)q, (float*)res, (const float*)tr_cur, (float*)tr_nxt, mapP, (const float*)geo,
-        (const float*)gface, (const float*)invM, bc, (float)tau, (float)rka, (float)rkb, (float)dt, write_traces);
+        (const float*)gface, (const float*)invM, bc, (float)tau, (float)rka, (float)rkb, (float)dt,
+        (const float*)dt_elem, write_traces);
   }
   static cudaError_t upload_c32(const double* tab) {
     using C = C32<N>;

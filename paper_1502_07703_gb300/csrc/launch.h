@@ -15,7 +15,7 @@ struct Launchers {
   void (*trace)(int64_t K, const void* q, const void* tab, void* tr, cudaStream_t s);
   void (*rhs_update)(int64_t K, void* q, void* res, const void* tr, const int32_t* mapP, const void* geo,
                      const void* gface, const void* invM, const void* tab, int bc, double tau, double rka, double rkb,
-                     double dt, cudaStream_t s);
+                     double dt, const void* dt_elem, cudaStream_t s);
   void (*rhs_out)(int64_t K, const void* q, void* rhs, const void* tr, const int32_t* mapP, const void* geo,
                   const void* gface, const void* invM, const void* tab, int bc, double tau, cudaStream_t s);
   void (*project)(int64_t K, const double* ev, const double* gtab, const double* tabd, int bc, double t, void* q,
@@ -26,7 +26,7 @@ struct Launchers {
   // the updated state, residual and (if write_traces) the new traces into tr_nxt.
   void (*stage32)(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
                   const void* geo, const void* gface, const void* invM, int bc, double tau, double rka, double rkb,
-                  double dt, int write_traces, int nblocks, cudaStream_t s);
+                  double dt, const void* dt_elem, int write_traces, int nblocks, cudaStream_t s);
   // Fill the FP32 stage kernel's constant tables on the current device from the
   // double reference tables (TabLayout); null for double.
   cudaError_t (*upload_c32)(const double* tab);

@@ -43,7 +43,10 @@ template <int N>
 struct S32 {
   using d = Dims<N>;
   static constexpr int NT = 128;
-  static constexpr int SU = 12 * d::n1 + 4;        // per-(a,b)-point stride of the b-pass output
+  // per-(a,b)-point stride of the b-pass output, padded per degree so that the column
+  // stores of the b pass and the point loads of the mixing pass avoid bank conflicts
+  static constexpr int kPad[8] = {0, 0, 2, 1, 1, 3, 3, 1};
+  static constexpr int SU = 12 * d::n1 + kPad[N];
   static constexpr int YS = (d::P3 + 3) / 4 * 4;   // padded row stride of Y and Z
   static constexpr int nY = d::P3 * YS;            // Y block per (field, level)
   // shared-memory layout (floats)
@@ -68,7 +71,7 @@ __global__ void __launch_bounds__(128)
     stage32_kernel(int64_t K, float* __restrict__ q, float* __restrict__ res, const float* __restrict__ tr_cur,
                    float* __restrict__ tr_nxt, const int32_t* __restrict__ mapP, const float* __restrict__ geo,
                    const float* __restrict__ gface, const float* __restrict__ invM, int bc, float tau, float rka,
-                   float rkb, float dt, int write_traces) {
+                   float rkb, float dt, const float* __restrict__ dt_elem, int write_traces) {
   using d = Dims<N>;
   using S = S32<N>;
   using C = C32<N>;
@@ -264,7 +267,8 @@ __global__ void __launch_bounds__(128)
       for (int c = 0; c < P3; ++c) acc = fmaf(lr[c], Zr[c], acc);
       const float rhs = -invM[e * Np + n] * acc;
       const int64_t gi = e * 4 * Np + x;
-      const float rnew = fmaf(rka, res[gi], dt * rhs);
+      const float dte = dt_elem ? dt_elem[e] : dt;  // per-element step when meshes are batched
+      const float rnew = fmaf(rka, res[gi], dte * rhs);
       res[gi] = rnew;
       const float unew = fmaf(rkb, rnew, s_u[x]);
       q[gi] = unew;
