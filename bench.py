@@ -279,6 +279,44 @@ def measure_batch(binding, steps, warmup, dev, count=256):
     return out
 
 
+def matched_accuracy(binding, dev, T=0.005):
+    """FP32 against FP64 at matched L2 error against the exact solution.
+
+    Both precisions run the same (mesh, N) cases to the same final time T from
+    the projected standing wave. Where the discretisation error is far above the
+    FP32 rounding floor (~1e-6, Sec. 4.3) both reach the same error, so the
+    time per unit of simulated time compares like with like; below the floor
+    only FP64 reaches the error, and the cheapest FP64 case that does is the
+    comparison point."""
+    import numpy as np
+    import torch
+    from paper_1502_07703_gb300.mesh import make_pyramid_mesh
+
+    rows = []
+    for nx, n in ((8, 2), (16, 2), (32, 2), (8, 3), (16, 3), (32, 3), (8, 4), (16, 4), (32, 4), (16, 5), (32, 5)):
+        v, e = make_pyramid_mesh(nx, delta=DELTA, seed=SEED)
+        for prec in ("f64", "f32"):
+            s = binding.Solver(v, e, n, precision=prec, device=dev)
+            dt0 = s.dt_cfl(0.5)
+            steps = int(np.ceil(T / dt0))
+            dt = T / steps
+            s.project(0.0)
+            s.step(1, dt)
+            s.project(0.0)
+            stream = torch.cuda.current_stream(dev)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            s.step(steps, dt)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = ev0.elapsed_time(ev1)
+            err = s.error()[1]
+            rows.append({"nx": nx, "N": n, "K": s.K, "precision": prec, "steps": steps, "l2_rel_error": err,
+                         "ms_per_unit_time": ms / T, "ms_total": ms})
+            s.close()
+    return {"T": T, "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -287,6 +325,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32 precision-form measurements")
+    ap.add_argument("--matched-accuracy", action="store_true",
+                    help="only run the FP32-vs-FP64 matched-accuracy sweep and print it as JSON")
     ap.add_argument("--nx", type=int, default=NX, help="hexes per axis (32 = the benchmark workload)")
     ap.add_argument("--degree", type=int, default=N, help="polynomial degree (4 = the benchmark workload)")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"],
@@ -308,6 +348,10 @@ def main():
     dev = local if torch.cuda.is_available() else 0
     torch.cuda.set_device(dev)
     device = torch.device("cuda", dev)
+    if args.matched_accuracy:
+        if rank == 0:
+            print(json.dumps(matched_accuracy(binding, dev)), flush=True)
+        return
     v, e = make_pyramid_mesh(args.nx, delta=DELTA, seed=SEED)
     nd, prec = args.degree, args.precision
     s = binding.Solver(v, e, nd, precision=prec, bc="wall", tau=1.0, device=dev)
