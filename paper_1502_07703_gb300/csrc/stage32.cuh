@@ -43,10 +43,7 @@ template <int N>
 struct S32 {
   using d = Dims<N>;
   static constexpr int NT = 128;
-  // per-(a,b)-point stride of the b-pass output, padded per degree so that the column
-  // stores of the b pass and the point loads of the mixing pass avoid bank conflicts
-  static constexpr int kPad[8] = {0, 0, 2, 1, 1, 3, 3, 1};
-  static constexpr int SU = 12 * d::n1 + kPad[N];
+  static constexpr int G = (d::n1 + 1) / 2;        // level groups {g, N-g}
   static constexpr int YS = (d::P3 + 3) / 4 * 4;   // padded row stride of Y and Z
   static constexpr int nY = d::P3 * YS;            // Y block per (field, level)
   // shared-memory layout (floats)
@@ -57,17 +54,20 @@ struct S32 {
   static constexpr size_t geo = u + 4 * d::Np;                   // 9 n2
   static constexpr size_t gf = geo + d::NGEO * d::n2;            // NGF
   static constexpr size_t Fs = gf + d::NGF;                      // 4 Nfc  [f][g]
-  static constexpr size_t U3 = Fs + 4 * d::Nfc;                  // n2 x SU  [pq][f][U,Ua,Ub][k]
-  static constexpr size_t Y = U3 + d::n2 * SU;                   // 4 n1 nY  [f][k][p'][q']
+  static constexpr size_t A = Fs + 4 * d::Nfc;                   // [f][row][p]: a pass of u_old
+  static constexpr size_t dA = A + 4 * d::nrow * d::n1;          // [f][row][p]: a pass, d/da
+  static constexpr size_t ZA = 4 * d::nrow * YS > 8 * d::nrow * d::n1 ? 4 * d::nrow * YS : 8 * d::nrow * d::n1;
+  static constexpr size_t Y = A + ZA;                            // 4 n1 nY  [f][k][p'][q']
   static constexpr size_t Af = Y + 4 * d::n1 * nY;               // 4 x 2 x nrow: A at a = -1, +1 of u_new
   static constexpr size_t total = Af + 8 * d::nrow;
-  static constexpr size_t Z = U3;                                // 4 nrow YS [f][row][p'] (U3 dead by then)
-  static_assert(4 * d::nrow * YS <= d::n2 * SU, "Z must fit in the U3 region");
+  static constexpr size_t Z = A;                                 // 4 nrow YS [f][row][p'] (A, dA dead by then)
+  // resident CTAs per SM the register budget is tuned for
+  static constexpr int MIN_BLOCKS = N <= 5 ? 8 : 4;
   static constexpr size_t bytes = total * sizeof(float);
 };
 
 template <int N>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
     stage32_kernel(int64_t K, float* __restrict__ q, float* __restrict__ res, const float* __restrict__ tr_cur,
                    float* __restrict__ tr_nxt, const int32_t* __restrict__ mapP, const float* __restrict__ geo,
                    const float* __restrict__ gface, const float* __restrict__ invM, int bc, float tau, float rka,
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(128)
   using S = S32<N>;
   using C = C32<N>;
   constexpr int n1 = d::n1, n2 = d::n2, P3 = d::P3, nrow = d::nrow, Np = d::Np, Nfc = d::Nfc;
-  constexpr int YS = S::YS, nY = S::nY, SU = S::SU;
+  constexpr int YS = S::YS, nY = S::nY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
   float* s_lx = sm + S::lx;
@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(128)
   float* s_geo = sm + S::geo;
   float* s_gf = sm + S::gf;
   float* s_Fs = sm + S::Fs;
-  float* s_U3 = sm + S::U3;
+  float* s_A = sm + S::A;
+  float* s_dA = sm + S::dA;
   float* s_Y = sm + S::Y;
   float* s_Af = sm + S::Af;
   float* s_Z = sm + S::Z;
@@ -124,20 +125,21 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
       for (int f = 0; f < 4; ++f) s_Fs[f * Nfc + g] = F[f];
     }
-    // ---- a and b passes per (field, a point p): registers hold the column
-    if (tid < 4 * n1) {
-      const int f = tid / n1, p = tid - f * n1;
+    // ---- a pass per (level group, field, a point p): A = l^k(a_p) u, dA = l^k'(a_p) u.
+    // Warp g takes levels g and N-g, whose (k+1)^2 costs pair up.
+    if ((tid & 31) < 4 * n1 && (tid >> 5) < S::G) {
+      const int grp = tid >> 5, lane = tid & 31;
+      const int f = lane / n1, p = lane - f * n1;
       const float* uf = s_u + f * Np;
-      float* out = s_U3 + f * 3 * n1;
 #pragma unroll
       for (int k = 0; k <= N; ++k) {
+        if (k != grp && k != N - grp) continue;
         float lxc[n1], dlc[n1];
 #pragma unroll
         for (int i = 0; i <= k; ++i) {
           lxc[i] = s_lx[(tri_num(k) + i) * P3 + p];
           dlc[i] = s_dl[(tri_num(k) + i) * n1 + p];
         }
-        float A[n1], dA[n1];
 #pragma unroll
         for (int j = 0; j <= k; ++j) {
           float a = 0.f, da = 0.f;
@@ -147,23 +149,9 @@ __global__ void __launch_bounds__(128)
             a = fmaf(c, lxc[i], a);
             da = fmaf(c, dlc[i], da);
           }
-          A[j] = a;
-          dA[j] = da;
-        }
-#pragma unroll
-        for (int qq = 0; qq <= N; ++qq) {
-          float u = 0.f, ua = 0.f, ub = 0.f;
-#pragma unroll
-          for (int j = 0; j <= k; ++j) {
-            const float l = c32[C::LX + (tri_num(k) + j) * P3 + qq];
-            u = fmaf(A[j], l, u);
-            ua = fmaf(dA[j], l, ua);
-            ub = fmaf(A[j], c32[C::DL + (tri_num(k) + j) * n1 + qq], ub);
-          }
-          float* o = out + (p + n1 * qq) * SU;
-          o[k] = u;
-          o[n1 + k] = ua;
-          o[2 * n1 + k] = ub;
+          const int o = (f * nrow + tri_num(k) + j) * n1 + p;
+          s_A[o] = a;
+          s_dA[o] = da;
         }
       }
     }
@@ -172,19 +160,44 @@ __global__ void __launch_bounds__(128)
     // ---- level mixing (c direction of Alg. 1) per (a,b) point, base lift; triangle-face c^T
     for (int x = tid; x < n2 + 16 * n1; x += S::NT) {
       if (x < n2) {
+        // b pass at this (a_p, b_q) point for all fields and levels, in registers
         const int pq = x, p = pq % n1, qq = pq / n1;
-        const float* Uq = s_U3 + pq * SU;
         const float* g = s_geo + pq * d::NGEO;
-        float X[n1], Zc[n1];
+        float lq[nrow], dlq[nrow];
+#pragma unroll
+        for (int r = 0; r < nrow; ++r) {
+          lq[r] = s_lx[r * P3 + qq];
+          dlq[r] = s_dl[r * n1 + qq];
+        }
+        float U0[n1], Ua0[n1], Ub0[n1], X[n1], Zc[n1];
 #pragma unroll
         for (int k = 0; k <= N; ++k) {
+          float u = 0.f, ua = 0.f, ub = 0.f;
+#pragma unroll
+          for (int j = 0; j <= k; ++j) {
+            const int o = (tri_num(k) + j) * n1 + p;
+            const float a = s_A[o], da = s_dA[o];
+            u = fmaf(a, lq[tri_num(k) + j], u);
+            ub = fmaf(a, dlq[tri_num(k) + j], ub);
+            ua = fmaf(da, lq[tri_num(k) + j], ua);
+          }
+          U0[k] = u;
+          Ua0[k] = ua;
+          Ub0[k] = ub;
           float xs = 0.f, zs = 0.f;
 #pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            const float* Um = Uq + (m + 1) * 3 * n1;
-            xs = fmaf(g[m], Um[n1 + k], xs);
-            xs = fmaf(g[3 + m], Um[2 * n1 + k], xs);
-            zs = fmaf(g[6 + m], Um[k], zs);
+          for (int m = 0; m < 3; ++m) {  // velocity fields: only the div combination is kept
+            float v = 0.f, va = 0.f, vb = 0.f;
+#pragma unroll
+            for (int j = 0; j <= k; ++j) {
+              const int o = ((m + 1) * nrow + tri_num(k) + j) * n1 + p;
+              const float a = s_A[o], da = s_dA[o];
+              v = fmaf(a, lq[tri_num(k) + j], v);
+              vb = fmaf(a, dlq[tri_num(k) + j], vb);
+              va = fmaf(da, lq[tri_num(k) + j], va);
+            }
+            xs = fmaf(g[m], va, fmaf(g[3 + m], vb, xs));
+            zs = fmaf(g[6 + m], v, zs);
           }
           X[k] = xs;
           Zc[k] = zs;
@@ -198,9 +211,9 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
           for (int k = 0; k <= N; ++k) {
             const float mh = c32[C::MH + kp * n1 + k], mg = c32[C::MG + kp * n1 + k];
-            al = fmaf(mh, Uq[n1 + k], al);
-            be = fmaf(mh, Uq[2 * n1 + k], be);
-            ga = fmaf(mg, Uq[k], ga);
+            al = fmaf(mh, Ua0[k], al);
+            be = fmaf(mh, Ub0[k], be);
+            ga = fmaf(mg, U0[k], ga);
             dv = fmaf(mh, X[k], fmaf(mg, Zc[k], dv));
           }
           const float gb = c32[C::GB + kp];
@@ -236,10 +249,12 @@ __global__ void __launch_bounds__(128)
     __syncthreads();
 
     // ---- b^T pass per (field, row p' of Y): Z[f][row(k,j)][p'] = sum_q' l_j^k(x_q') Y[f][k][p'][q']
-    if (tid < 4 * P3) {
-      const int f = tid / P3, pp = tid - f * P3;
+    for (int x = tid; x < S::G * 4 * P3; x += S::NT) {
+      const int grp = x / (4 * P3), y = x - grp * 4 * P3;
+      const int f = y / P3, pp = y - f * P3;
 #pragma unroll
       for (int k = 0; k <= N; ++k) {
+        if (k != grp && k != N - grp) continue;
         const float* Yr = s_Y + (f * n1 + k) * nY + pp * YS;
         float yv[P3];
 #pragma unroll
