@@ -138,7 +138,7 @@ def _face_tangents(f, Jac):
 class PyramidDG:
     """Dense-matrix DG discretisation on a pyramid mesh (state arrays (K, 4, Np), psi basis)."""
 
-    def __init__(self, vertices, EToV, N, tau=1.0, bc="wall", chunk=512):
+    def __init__(self, vertices, EToV, N, tau=1.0, bc="wall", chunk=512, periodic=None):
         self.N = int(N)
         self.Np = num_modes(self.N)
         self.tau = float(tau)
@@ -198,11 +198,19 @@ class PyramidDG:
             self.nrm[:, f] = ns / sJ[..., None]
         self.fw = np.stack([fr["w"] for fr in self.frules])  # (5, nf)
 
-        # connectivity: match face points by physical coordinates
+        # connectivity: match face points by physical coordinates; with periodic = (lo, hi)
+        # the box [lo, hi]^3 is a torus and points are matched modulo its period
         pts = self.Xf.reshape(-1, 3)
         hmin = np.cbrt(np.min(np.einsum("q,kq->k", w, self.J)))
         tol = 1e-8 * hmin
-        tree = cKDTree(pts)
+        if periodic is not None:
+            lo, hi = float(periodic[0]), float(periodic[1])
+            L = hi - lo
+            pts = np.mod(pts - lo, L)
+            pts = np.where(pts > L - 1e-9 * L, 0.0, pts)
+            tree = cKDTree(pts, boxsize=L)
+        else:
+            tree = cKDTree(pts)
         dist, idx = tree.query(pts, k=2)
         mapP = np.where(dist[:, 1] < tol, idx[:, 1], -1)
         # the nearest point is the point itself unless two coincide exactly
