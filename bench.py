@@ -241,6 +241,40 @@ def workload_name(nx, n, prec):
             f"N={n} (Np={num_modes(n)}), 4 fields, upwind flux, rigid wall, standing wave, LSRK4 at CFL 0.5, {prec}")
 
 
+def measure_advection(binding, nx, n, precision, steps, warmup, dev):
+    """Scalar advection (Sec. 4.1): u_t + div(beta u) = 0, beta = (1, 0, 0), upwind alpha-flux,
+    periodic unit cube cut into nx^3 hexes x 6 pyramids (+-0.05h, seed 1)."""
+    import torch
+    from paper_1502_07703_gb300.mesh import make_pyramid_mesh
+
+    v, e = make_pyramid_mesh(nx, delta=DELTA, seed=SEED)
+    s = binding.Solver(v, e, n, precision=precision, tau=1.0, device=dev, equation="advection",
+                       beta=(1.0, 0.0, 0.0), periodic=(0.0, 1.0))
+    dt = s.dt_cfl(0.5)
+    s.project(0.0)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(warmup):
+        s.step(1, dt)
+    s.sync()
+    s.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        s.step(1, dt)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1)
+    prof = s.profile_read()
+    s.profile(False)
+    out = {"equation": "advection", "mesh": f"{nx}^3 hexes x 6, periodic", "K": s.K, "N": n, "Np": s.Np,
+           "precision": precision, "steps": steps, "ms_per_step": ms / steps,
+           "dof_updates_per_s_per_stage": s.K * s.Np * 5 * steps / (ms * 1e-3),
+           "stage_kernel_ms": prof["rhs"][0] / prof["rhs"][1], "trace_kernel_ms": prof["trace"][0] / prof["trace"][1],
+           "l2_rel_error_vs_exact": s.error()[1]}
+    s.close()
+    return out
+
+
 def measure_batch(binding, steps, warmup, dev, count=256):
     """Batching form: `count` independent meshes (sizes log-uniform 48..49,152 pyramids,
     degrees uniform in 2..6, seed 2), FP32, each with its own CFL time step, advanced by
@@ -432,6 +466,8 @@ def main():
                                              (NX, DELTA, SEED, 7, "f32", 10), (64, 0.1, 3, 5, "f32", 10)):
             forms.append(measure_form(binding, nx, delta, seed, n, prec, st, 2, dev))
         forms.append(measure_batch(binding, 10, 2, dev))
+        forms.append(measure_advection(binding, NX, 4, "f64", 10, 2, dev))
+        forms.append(measure_advection(binding, NX, 4, "f32", 20, 2, dev))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

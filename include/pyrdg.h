@@ -23,7 +23,8 @@
  *    quadrilateral with (v2-v1) x (v4-v1) pointing toward the apex v5, v3
  *    opposite v1 (the images of (-1,-1,-1), (1,-1,-1), (1,1,-1), (-1,1,-1),
  *    (-1,-1,1)).
- *  - State layout: row-major [K][4][Np], fields (p, u, v, w), Np =
+ *  - State layout: row-major [K][nf][Np]; nf = 4 fields (p, u, v, w) for the wave
+ *    equation, nf = 1 (u) for advection (pyr_dg_num_fields); Np =
  *    (N+1)(N+2)(2N+3)/6 coefficients of the semi-nodal basis per field, in
  *    the order n = k(k+1)(2k+1)/6 + j(k+1) + i for phi_ijk =
  *    l_i^k(a) l_j^k(b) ((1-c)/2)^k P_{N-k}^{(2k+3,0)}(c), l^k the Lagrange
@@ -59,6 +60,7 @@ enum { PYR_DG_MIN_N = 1, PYR_DG_MAX_N = 7 };
 enum { PYR_DG_F64 = 0, PYR_DG_F32 = 1 };
 enum { PYR_DG_BC_WALL = 0, PYR_DG_BC_FREE = 1 };
 enum { PYR_DG_HOST = 0, PYR_DG_DEVICE = 1 };
+enum { PYR_DG_WAVE = 0, PYR_DG_ADVECTION = 1 };
 
 typedef struct pyr_dg pyr_dg; /* opaque handle, owned by the library */
 
@@ -72,9 +74,18 @@ typedef struct pyr_dg_opts {
   double tau;     /* flux penalty of Sec. 4.3: 1 = upwind, 0 = central; >= 0 */
   void* stream;   /* cudaStream_t for all work of this handle; NULL = default */
   int device;     /* CUDA device ordinal; -1 = the calling thread's current device */
+  int equation;   /* PYR_DG_WAVE: the acoustic system (p, u, v, w), 4 fields.
+                     PYR_DG_ADVECTION: u_t + div(beta u) = 0 of Sec. 4.1, 1 field, with
+                     the alpha-flux ((beta_n - alpha|beta_n|)/2)(u+ - u-), alpha = tau
+                     (1 upwind, 0 central); needs periodic = 1 */
+  double beta[3]; /* advection velocity (PYR_DG_ADVECTION) */
+  int periodic;   /* 1: the box [box_lo, box_hi]^3 is periodic: faces on opposite boundary
+                     planes are neighbours (their vertices must coincide modulo the period) */
+  double box_lo, box_hi;
 } pyr_dg_opts;
 
-/* Fill *opts with: F64, wall, tau = 1, stream NULL, device -1. */
+/* Fill *opts with: F64, wall, tau = 1, stream NULL, device -1, wave equation,
+ * beta = (1, 0, 0), not periodic, box [0, 1]. */
 void pyr_dg_default_opts(pyr_dg_opts* opts);
 
 /* Build a solver for one mesh (Sec. 2 vertex maps, Sec. 4.1 cubature).
@@ -95,11 +106,15 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
  * face cubature points per element Nfc = 5(N+1)^2, precision. Any pointer may be NULL. */
 int pyr_dg_info(const pyr_dg* h, int64_t* K, int* N, int* Np, int* Nfc, int* precision);
 
+/* Fields per element of the state: 4 (wave) or 1 (advection). */
+int pyr_dg_num_fields(const pyr_dg* h, int* nf);
+
 /* L2 projection (volume rule of Sec. 4.1, diagonal mass of Lemma 3) of the
  * exact standing wave at time t0 into the state; sets the time to t0 and
  * zeroes the LSRK residual. 'wall': p = cos(pi x)cos(pi y)cos(pi z)cos(sqrt3 pi t),
  * u = sin(pi x)cos(pi y)cos(pi z)sin(sqrt3 pi t)/sqrt3 (cyclic), for [0,1]^3;
- * 'free': the resonant cavity of Sec. 4.3 on [-1,1]^3. Asynchronous. */
+ * 'free': the resonant cavity of Sec. 4.3 on [-1,1]^3. Advection: u0(x - beta t) with
+ * u0 = sin(2 pi X) cos(2 pi Y) sin(2 pi Z), X = (x - box_lo)/(box_hi - box_lo). Asynchronous. */
 int pyr_dg_project(pyr_dg* h, double t0);
 
 /* Copy a state in (set) or out (get). q: K*4*Np elements of the handle's
@@ -235,6 +250,12 @@ int pyr_dg_host_gauss_jacobi(int n, double alpha, double beta, double* x, double
  * nboundary (may be NULL) receives the number of boundary faces. */
 int pyr_dg_host_connectivity(const double* vertices, int64_t Nv, const int32_t* EToV, int64_t K, int N,
                              int64_t* mapP, int64_t* nboundary);
+
+/* As pyr_dg_host_connectivity, with the box [box_lo, box_hi]^3 periodic: faces on
+ * opposite boundary planes are matched as neighbours (cubature points compared
+ * modulo the period). */
+int pyr_dg_host_connectivity_periodic(const double* vertices, int64_t Nv, const int32_t* EToV, int64_t K, int N,
+                                      double box_lo, double box_hi, int64_t* mapP, int64_t* nboundary);
 
 /* Measured FMA throughput of this GPU in TFLOP/s (2 flops per FMA) for
  * precision PYR_DG_F64 or PYR_DG_F32: a register-only kernel of independent

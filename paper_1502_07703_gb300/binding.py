@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libpyrdg.so")
 PYR_DG_F64, PYR_DG_F32 = 0, 1
 PYR_DG_BC_WALL, PYR_DG_BC_FREE = 0, 1
 PYR_DG_HOST, PYR_DG_DEVICE = 0, 1
+PYR_DG_WAVE, PYR_DG_ADVECTION = 0, 1
 ERRORS = {-1: "BAD_ARG", -2: "BAD_MESH", -3: "UNSUPPORTED_N", -4: "CUDA", -5: "NO_MEMORY"}
 
 _lib = None
@@ -37,6 +38,11 @@ class Opts(ctypes.Structure):
         ("tau", ctypes.c_double),
         ("stream", ctypes.c_void_p),
         ("device", ctypes.c_int),
+        ("equation", ctypes.c_int),
+        ("beta", ctypes.c_double * 3),
+        ("periodic", ctypes.c_int),
+        ("box_lo", ctypes.c_double),
+        ("box_hi", ctypes.c_double),
     ]
 
 
@@ -66,6 +72,9 @@ _SIGNATURES = {
     "pyr_dg_host_connectivity": (ctypes.c_int, [_c_dp, ctypes.c_int64, _c_i32p, ctypes.c_int64, ctypes.c_int,
                                                 _c_i64p, _c_i64p]),
     "pyr_dg_fma_peak": (ctypes.c_int, [ctypes.c_int, _c_dp]),
+    "pyr_dg_num_fields": (ctypes.c_int, [_c_h, _c_ip]),
+    "pyr_dg_host_connectivity_periodic": (ctypes.c_int, [_c_dp, ctypes.c_int64, _c_i32p, ctypes.c_int64, ctypes.c_int,
+                                                         ctypes.c_double, ctypes.c_double, _c_i64p, _c_i64p]),
     "pyr_dg_rhs_noalloc": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_void_p]),
     "pyr_dg_profile": (ctypes.c_int, [_c_h, ctypes.c_int]),
     "pyr_dg_batch_setup": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_c_dp), _c_i64p, ctypes.POINTER(_c_i32p),
@@ -130,6 +139,19 @@ def connectivity(vertices, EToV, N):
     return mapP, nb.value
 
 
+def connectivity_periodic(vertices, EToV, N, box=(0.0, 1.0)):
+    """The library's host face connectivity on the periodic box [lo, hi]^3."""
+    V = np.ascontiguousarray(vertices, dtype=np.float64)
+    E = np.ascontiguousarray(EToV, dtype=np.int32)
+    K = E.shape[0]
+    mapP = np.empty(K * 5 * (N + 1) ** 2, dtype=np.int64)
+    nb = ctypes.c_int64(0)
+    _check(lib().pyr_dg_host_connectivity_periodic(_ptr(V, ctypes.c_double), V.shape[0], _ptr(E, ctypes.c_int32), K,
+                                                   N, float(box[0]), float(box[1]), _ptr(mapP, ctypes.c_int64),
+                                                   ctypes.byref(nb)))
+    return mapP, nb.value
+
+
 def fma_peak(precision="f64"):
     """Measured FMA throughput of the current GPU in TFLOP/s."""
     out = ctypes.c_double(0.0)
@@ -141,7 +163,9 @@ class Solver:
     """One mesh advanced by the library. State arrays are (K, 4, Np) in the
     handle's precision, semi-nodal coefficients (layout in include/pyrdg.h)."""
 
-    def __init__(self, vertices, EToV, N, precision="f64", bc="wall", tau=1.0, stream=None, device=None):
+    def __init__(self, vertices, EToV, N, precision="f64", bc="wall", tau=1.0, stream=None, device=None,
+                 equation="wave", beta=(1.0, 0.0, 0.0), periodic=None):
+        """equation: "wave" (4 fields) or "advection" (1 field, needs periodic=(lo, hi); tau is alpha)."""
         import torch
 
         self._torch = torch
@@ -154,6 +178,12 @@ class Solver:
         o.precision = {"f64": PYR_DG_F64, "f32": PYR_DG_F32}[precision]
         o.bc = {"wall": PYR_DG_BC_WALL, "free": PYR_DG_BC_FREE}[bc]
         o.tau = float(tau)
+        o.equation = {"wave": PYR_DG_WAVE, "advection": PYR_DG_ADVECTION}[equation]
+        for m in range(3):
+            o.beta[m] = float(beta[m])
+        if periodic is not None:
+            o.periodic = 1
+            o.box_lo, o.box_hi = float(periodic[0]), float(periodic[1])
         if device is None:
             device = torch.cuda.current_device() if torch.cuda.is_available() else 0
         o.device = int(device)
@@ -172,6 +202,10 @@ class Solver:
         _check(lib().pyr_dg_info(h, ctypes.byref(K), ctypes.byref(n), ctypes.byref(Np), ctypes.byref(Nfc),
                                  ctypes.byref(prec)))
         self.K, self.N, self.Np, self.Nfc = K.value, n.value, Np.value, Nfc.value
+        nf = ctypes.c_int()
+        _check(lib().pyr_dg_num_fields(h, ctypes.byref(nf)))
+        self.nf = nf.value
+        self.equation = equation
         self.np_dtype = np.float64 if precision == "f64" else np.float32
         self.torch_dtype = torch.float64 if precision == "f64" else torch.float32
 
@@ -195,7 +229,7 @@ class Solver:
 
     @property
     def shape(self):
-        return (self.K, 4, self.Np)
+        return (self.K, self.nf, self.Np)
 
     # -- calls
     def project(self, t0=0.0):

@@ -98,7 +98,23 @@ void free_all(pyr_dg* h) {
 
 namespace pyrdg {
 int enqueue_steps(pyr_dg* h, int nsteps, double dt) {
-  if (h->L->stage32 && nsteps > 0) {
+  if (h->equation == PYR_DG_ADVECTION) {
+    for (int n = 0; n < nsteps; ++n) {
+      for (int s = 0; s < 5; ++s) {
+        size_t slot = 0;
+        CUDA_TRY(prof_begin(h, 0, &slot));
+        h->L->trace1(h->K, h->q, h->tab, h->tr, h->stream);
+        CUDA_TRY(prof_end(h, slot));
+        CUDA_TRY(prof_begin(h, 1, &slot));
+        h->L->rhs1(h->K, h->q, h->q, h->res, h->tr, h->mapP, h->geo, h->gface, h->invM, h->tab, h->beta, h->tau,
+                   kRkA[s], kRkB[s], dt, 1, h->stream);
+        CUDA_TRY(prof_end(h, slot));
+      }
+    }
+    CUDA_TRY(cudaGetLastError());
+    return PYR_DG_OK;
+  }
+  if (h->use_stage32 && nsteps > 0) {
     // FP32: one launch per stage; traces ping-pong between tr and tr2
     void* buf[2] = {h->tr, h->tr2};
     size_t slot = 0;
@@ -146,6 +162,13 @@ void pyr_dg_default_opts(pyr_dg_opts* o) {
   o->tau = 1.0;
   o->stream = nullptr;
   o->device = -1;
+  o->equation = PYR_DG_WAVE;
+  o->beta[0] = 1.0;
+  o->beta[1] = 0.0;
+  o->beta[2] = 0.0;
+  o->periodic = 0;
+  o->box_lo = 0.0;
+  o->box_hi = 1.0;
 }
 
 const char* pyr_dg_last_error(void) { return g_err.c_str(); }
@@ -169,6 +192,20 @@ int pyr_dg_host_connectivity(const double* vertices, int64_t Nv, const int32_t* 
   return PYR_DG_OK;
 }
 
+int pyr_dg_host_connectivity_periodic(const double* vertices, int64_t Nv, const int32_t* EToV, int64_t K, int N,
+                                      double box_lo, double box_hi, int64_t* mapP, int64_t* nboundary) {
+  if (!vertices || !EToV || !mapP || Nv < 1 || K < 1 || !(box_hi > box_lo))
+    return fail(PYR_DG_ERR_BAD_ARG, "bad connectivity arguments");
+  if (N < PYR_DG_MIN_N || N > PYR_DG_MAX_N) return fail(PYR_DG_ERR_UNSUPPORTED_N, "N = %d unsupported", N);
+  std::vector<int64_t> m;
+  std::string err;
+  const double box[2] = {box_lo, box_hi};
+  const int rc = pyrdg::build_connectivity(vertices, Nv, EToV, K, N, m, nboundary, err, box);
+  if (rc != 0) return fail(PYR_DG_ERR_BAD_MESH, "%s", err.c_str());
+  std::memcpy(mapP, m.data(), m.size() * sizeof(int64_t));
+  return PYR_DG_OK;
+}
+
 int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_t K, int N, const pyr_dg_opts* opts,
                  pyr_dg** out) {
   g_err.clear();
@@ -186,6 +223,13 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   if (o.precision != PYR_DG_F64 && o.precision != PYR_DG_F32) return fail(PYR_DG_ERR_BAD_ARG, "unknown precision");
   if (o.bc != PYR_DG_BC_WALL && o.bc != PYR_DG_BC_FREE) return fail(PYR_DG_ERR_BAD_ARG, "unknown bc");
   if (!(o.tau >= 0.0) || !std::isfinite(o.tau)) return fail(PYR_DG_ERR_BAD_ARG, "tau must be finite and >= 0");
+  if (o.equation != PYR_DG_WAVE && o.equation != PYR_DG_ADVECTION) return fail(PYR_DG_ERR_BAD_ARG, "unknown equation");
+  if (o.periodic && !(o.box_hi > o.box_lo)) return fail(PYR_DG_ERR_BAD_ARG, "periodic box needs box_hi > box_lo");
+  if (o.equation == PYR_DG_ADVECTION && !o.periodic)
+    return fail(PYR_DG_ERR_BAD_ARG, "advection is implemented on periodic boxes only (set periodic = 1)");
+  if (o.equation == PYR_DG_ADVECTION &&
+      !(std::isfinite(o.beta[0]) && std::isfinite(o.beta[1]) && std::isfinite(o.beta[2])))
+    return fail(PYR_DG_ERR_BAD_ARG, "beta must be finite");
   const int n1 = N + 1, n2 = n1 * n1, Nfc = 5 * n2, Np = pyrdg::num_modes(N);
   if (K * (int64_t)Nfc > 0x7fffffffLL) return fail(PYR_DG_ERR_BAD_ARG, "K * Nfc exceeds int32 face indexing");
 
@@ -195,8 +239,12 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   std::vector<int64_t> map64;
   std::string err;
   int64_t nbnd = 0;
-  if (pyrdg::build_connectivity(vertices, Nv, EToV, K, N, map64, &nbnd, err) != 0)
+  const double box[2] = {o.box_lo, o.box_hi};
+  if (pyrdg::build_connectivity(vertices, Nv, EToV, K, N, map64, &nbnd, err, o.periodic ? box : nullptr) != 0)
     return fail(PYR_DG_ERR_BAD_MESH, "%s", err.c_str());
+  if (o.equation == PYR_DG_ADVECTION && nbnd > 0)
+    return fail(PYR_DG_ERR_BAD_MESH, "advection needs every face matched, %lld faces are unmatched on the periodic box",
+                (long long)nbnd);
   std::vector<double> ev((size_t)K * 15);
   const pyrdg::GeoLayout G(N);
   double max_aov = 0.0;
@@ -225,6 +273,11 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   h->precision = o.precision;
   h->bc = o.bc;
   h->tau = o.tau;
+  h->equation = o.equation;
+  h->nf = o.equation == PYR_DG_ADVECTION ? 1 : 4;
+  for (int m = 0; m < 3; ++m) h->beta[m] = o.beta[m];
+  h->box_lo = o.box_lo;
+  h->box_hi = o.box_hi;
   h->tsize = o.precision == PYR_DG_F64 ? 8 : 4;
   h->stream = (cudaStream_t)o.stream;
   h->max_aov = max_aov;
@@ -245,7 +298,8 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   h->err_blocks = (int)std::min<int64_t>(K, (int64_t)(nsm > 0 ? nsm : 1) * 4);
 
   const size_t ts = h->tsize;
-  const size_t stateB = (size_t)K * 4 * Np * ts;
+  h->use_stage32 = h->L->stage32 != nullptr && h->equation == PYR_DG_WAVE;
+  const size_t stateB = (size_t)K * h->nf * Np * ts;
   const pyrdg::TabLayout TL(N);
   struct Alloc {
     void** p;
@@ -263,7 +317,7 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
       {(void**)&h->ev, (size_t)K * 15 * 8},
       {(void**)&h->partial, (size_t)h->err_blocks * 2 * 8},
       {(void**)&h->mapP, (size_t)K * Nfc * 4},
-      {&h->tr2, h->L->stage32 ? (size_t)K * Nfc * 4 * ts : 0},
+      {&h->tr2, h->use_stage32 ? (size_t)K * Nfc * 4 * ts : 0},
   };
   for (auto& a : allocs) {
     if (a.bytes == 0) continue;
@@ -284,7 +338,7 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   cudaError_t e = cudaSuccess;
   cudaStream_t s = h->stream;
   if (e == cudaSuccess) e = h->L->prepare();
-  if (e == cudaSuccess && h->L->upload_c32) {
+  if (e == cudaSuccess && h->use_stage32) {
     e = h->L->upload_c32(T.tab.data());
     h->stage_blocks = (int)std::min<int64_t>(K, (int64_t)(nsm > 0 ? nsm : 1) * h->L->blocks_per_sm32());
   }
@@ -319,14 +373,23 @@ int pyr_dg_info(const pyr_dg* h, int64_t* K, int* N, int* Np, int* Nfc, int* pre
   return PYR_DG_OK;
 }
 
+int pyr_dg_num_fields(const pyr_dg* h, int* nf) {
+  if (!h || !nf) return fail(PYR_DG_ERR_BAD_ARG, "null argument");
+  *nf = h->nf;
+  return PYR_DG_OK;
+}
+
 int pyr_dg_project(pyr_dg* h, double t0) {
   if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
   if (!std::isfinite(t0)) return fail(PYR_DG_ERR_BAD_ARG, "t0 must be finite");
   DeviceGuard g(h->device);
   CUDA_TRY(g.err);
-  h->L->project(h->K, h->ev, h->gtab, h->tabd, h->bc, t0, h->q, h->stream);
+  if (h->equation == PYR_DG_ADVECTION)
+    h->L->project1(h->K, h->ev, h->gtab, h->tabd, h->beta, h->box_lo, h->box_hi - h->box_lo, t0, h->q, h->stream);
+  else
+    h->L->project(h->K, h->ev, h->gtab, h->tabd, h->bc, t0, h->q, h->stream);
   CUDA_TRY(cudaGetLastError());
-  CUDA_TRY(cudaMemsetAsync(h->res, 0, (size_t)h->K * 4 * h->Np * h->tsize, h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->res, 0, (size_t)h->K * h->nf * h->Np * h->tsize, h->stream));
   h->t = t0;
   h->tr_valid = false;
   return PYR_DG_OK;
@@ -337,7 +400,7 @@ int pyr_dg_set_state(pyr_dg* h, const void* q, int where, double t) {
   if (where != PYR_DG_HOST && where != PYR_DG_DEVICE) return fail(PYR_DG_ERR_BAD_ARG, "bad `where`");
   DeviceGuard g(h->device);
   CUDA_TRY(g.err);
-  const size_t bytes = (size_t)h->K * 4 * h->Np * h->tsize;
+  const size_t bytes = (size_t)h->K * h->nf * h->Np * h->tsize;
   CUDA_TRY(cudaMemcpyAsync(h->q, q, bytes, where == PYR_DG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                            h->stream));
   CUDA_TRY(cudaMemsetAsync(h->res, 0, bytes, h->stream));
@@ -352,7 +415,7 @@ int pyr_dg_get_state(pyr_dg* h, void* q, int where) {
   if (where != PYR_DG_HOST && where != PYR_DG_DEVICE) return fail(PYR_DG_ERR_BAD_ARG, "bad `where`");
   DeviceGuard g(h->device);
   CUDA_TRY(g.err);
-  const size_t bytes = (size_t)h->K * 4 * h->Np * h->tsize;
+  const size_t bytes = (size_t)h->K * h->nf * h->Np * h->tsize;
   CUDA_TRY(cudaMemcpyAsync(q, h->q, bytes, where == PYR_DG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
                            h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -364,8 +427,15 @@ int pyr_dg_rhs(pyr_dg* h, const void* q_dev, void* rhs_dev) {
   if (q_dev == rhs_dev) return fail(PYR_DG_ERR_BAD_ARG, "rhs must not alias q");
   DeviceGuard g(h->device);
   CUDA_TRY(g.err);
-  h->L->trace(h->K, q_dev, h->tab, h->tr, h->stream);
-  h->L->rhs_out(h->K, q_dev, rhs_dev, h->tr, h->mapP, h->geo, h->gface, h->invM, h->tab, h->bc, h->tau, h->stream);
+  if (h->equation == PYR_DG_ADVECTION) {
+    h->L->trace1(h->K, q_dev, h->tab, h->tr, h->stream);
+    h->L->rhs1(h->K, q_dev, rhs_dev, nullptr, h->tr, h->mapP, h->geo, h->gface, h->invM, h->tab, h->beta, h->tau, 0.0,
+               0.0, 0.0, 0, h->stream);
+  } else {
+    h->L->trace(h->K, q_dev, h->tab, h->tr, h->stream);
+    h->L->rhs_out(h->K, q_dev, rhs_dev, h->tr, h->mapP, h->geo, h->gface, h->invM, h->tab, h->bc, h->tau,
+                  h->stream);
+  }
   CUDA_TRY(cudaGetLastError());
   h->tr_valid = false;  // the trace buffer was used as scratch
   return PYR_DG_OK;
@@ -386,7 +456,11 @@ int pyr_dg_error(pyr_dg* h, double* l2_abs, double* l2_rel) {
   if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
   DeviceGuard g(h->device);
   CUDA_TRY(g.err);
-  h->L->error(h->K, h->q, h->ev, h->gtab, h->bc, h->t, h->partial, h->err_blocks, h->stream);
+  if (h->equation == PYR_DG_ADVECTION)
+    h->L->error1(h->K, h->q, h->ev, h->gtab, h->beta, h->box_lo, h->box_hi - h->box_lo, h->t, h->partial,
+                 h->err_blocks, h->stream);
+  else
+    h->L->error(h->K, h->q, h->ev, h->gtab, h->bc, h->t, h->partial, h->err_blocks, h->stream);
   CUDA_TRY(cudaGetLastError());
   std::vector<double> part((size_t)h->err_blocks * 2);
   CUDA_TRY(cudaMemcpyAsync(part.data(), h->partial, part.size() * 8, cudaMemcpyDeviceToHost, h->stream));
@@ -405,7 +479,11 @@ int pyr_dg_dt_cfl(pyr_dg* h, double cfl, double* dt) {
   if (!h || !dt) return fail(PYR_DG_ERR_BAD_ARG, "null argument");
   if (!(cfl > 0.0)) return fail(PYR_DG_ERR_BAD_ARG, "cfl must be > 0");
   const double CN = 2.0 * (h->N + 1) * (h->N + 3) / 3.0;
-  *dt = cfl / (CN * h->max_aov);
+  double speed = 1.0;  // wave speed c = 1; advection: |beta|
+  if (h->equation == PYR_DG_ADVECTION)
+    speed = std::sqrt(h->beta[0] * h->beta[0] + h->beta[1] * h->beta[1] + h->beta[2] * h->beta[2]);
+  if (!(speed > 0.0)) return fail(PYR_DG_ERR_BAD_ARG, "advection speed is zero");
+  *dt = cfl / (CN * h->max_aov * speed);
   return PYR_DG_OK;
 }
 
@@ -477,6 +555,7 @@ void* g_noalloc_addr[kMaxNoallocDevices] = {};
 extern "C" int pyr_dg_rhs_noalloc(pyr_dg* h, const void* q_dev, void* rhs_dev) {
   if (!h || !q_dev || !rhs_dev) return fail(PYR_DG_ERR_BAD_ARG, "null argument");
   if (q_dev == rhs_dev) return fail(PYR_DG_ERR_BAD_ARG, "rhs must not alias q");
+  if (h->equation != PYR_DG_WAVE) return fail(PYR_DG_ERR_BAD_ARG, "pyr_dg_rhs_noalloc supports wave handles only");
   const size_t need = (size_t)h->K * h->Nfc * 4 * h->tsize;
   if (need > (size_t)PYR_DG_NOALLOC_SCRATCH_BYTES)
     return fail(PYR_DG_ERR_BAD_ARG,

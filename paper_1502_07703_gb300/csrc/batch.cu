@@ -83,6 +83,7 @@ int pyr_dg_batch_setup(int nmesh, const double* const* vertices, const int64_t* 
   pyr_dg_opts o;
   pyr_dg_default_opts(&o);
   if (opts) o = *opts;
+  if (o.equation != PYR_DG_WAVE) return fail(PYR_DG_ERR_BAD_ARG, "batches hold acoustic-wave meshes only");
   for (int i = 0; i < nmesh; ++i) {
     if (!vertices[i] || !EToV[i] || Nv[i] < 5 || K[i] < 1)
       return fail(PYR_DG_ERR_BAD_ARG, "mesh %d: null arrays or empty sizes", i);
@@ -176,7 +177,7 @@ int pyr_dg_batch_setup(int nmesh, const double* const* vertices, const int64_t* 
       return fail(PYR_DG_ERR_NO_MEMORY, "cannot allocate the per-element time steps");
     }
     // Autotune the persistent grid of the FP32 stage kernel on the zero state.
-    if (h->L->stage32 && h->K >= 4096) {
+    if (h->use_stage32 && h->K >= 4096) {
       int nsm = 1;
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
       const int maxb = std::max(1, h->stage_blocks / std::max(1, nsm));
@@ -228,7 +229,7 @@ int pyr_dg_batch_group_info(const pyr_dg_batch* b, int group, int* N, int64_t* K
   const pyr_dg* h = b->groups[group];
   if (N) *N = h->N;
   if (K) *K = h->K;
-  if (stage_blocks) *stage_blocks = h->L->stage32 ? h->stage_blocks : (int)h->K;
+  if (stage_blocks) *stage_blocks = h->use_stage32 ? h->stage_blocks : (int)h->K;
   return PYR_DG_OK;
 }
 

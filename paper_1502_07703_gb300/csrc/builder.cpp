@@ -311,9 +311,49 @@ struct FaceKey {
   bool same(const FaceKey& o) const { return v[0] == o.v[0] && v[1] == o.v[1] && v[2] == o.v[2] && v[3] == o.v[3]; }
 };
 
+// Canonical vertex ids for a box [lo, hi]^3 made periodic: a vertex on an upper
+// boundary plane is identified with its image on the lower plane (and so on for
+// edges and corners); every other vertex is its own representative.
+static void periodic_canonical(const double* V, int64_t Nv, double lo, double hi, std::vector<int64_t>& canon) {
+  const double L = hi - lo, tol = 1e-9 * L;
+  canon.resize((size_t)Nv);
+  struct Key {
+    int64_t q[3];
+    bool operator<(const Key& o) const {
+      return q[0] != o.q[0] ? q[0] < o.q[0] : (q[1] != o.q[1] ? q[1] < o.q[1] : q[2] < o.q[2]);
+    }
+  };
+  std::vector<std::pair<Key, int64_t>> keys;
+  for (int64_t v = 0; v < Nv; ++v) {
+    canon[(size_t)v] = v;
+    bool on_bnd = false;
+    Key k;
+    for (int m = 0; m < 3; ++m) {
+      double x = V[v * 3 + m] - lo;
+      if (std::fabs(x) < tol || std::fabs(x - L) < tol) on_bnd = true;
+      if (std::fabs(x - L) < tol) x = 0.0;
+      k.q[m] = (int64_t)std::llround(x / L * 1e8);
+    }
+    if (on_bnd) keys.push_back({k, v});
+  }
+  std::sort(keys.begin(), keys.end(), [](const std::pair<Key, int64_t>& a, const std::pair<Key, int64_t>& b) {
+    return a.first < b.first || (!(b.first < a.first) && a.second < b.second);
+  });
+  for (size_t i = 0; i < keys.size();) {
+    size_t j = i + 1;
+    while (j < keys.size() && !(keys[i].first < keys[j].first) && !(keys[j].first < keys[i].first)) ++j;
+    for (size_t t = i; t < j; ++t) canon[(size_t)keys[t].second] = keys[i].second;
+    i = j;
+  }
+}
+
 int build_connectivity(const double* V, int64_t Nv, const int32_t* EToV, int64_t K, int N,
-                       std::vector<int64_t>& mapP, int64_t* nbnd, std::string& err) {
+                       std::vector<int64_t>& mapP, int64_t* nbnd, std::string& err, const double* period_box) {
   const int n1 = N + 1, n2 = n1 * n1, Nfc = 5 * n2;
+  std::vector<int64_t> canon;
+  const bool periodic = period_box != nullptr;
+  const double pL = periodic ? period_box[1] - period_box[0] : 1.0;
+  if (periodic) periodic_canonical(V, Nv, period_box[0], period_box[1], canon);
   std::vector<double> xg(n1), wg(n1), xf(n1), wf(n1);
   gauss_jacobi(n1, 0.0, 0.0, xg.data(), wg.data());
   gauss_jacobi(n1, 1.0, 0.0, xf.data(), wf.data());
@@ -331,7 +371,14 @@ int build_connectivity(const double* V, int64_t Nv, const int32_t* EToV, int64_t
     for (int f = 0; f < 5; ++f) {
       FaceKey& k = keys[(size_t)e * 5 + f];
       const int nv = f == 0 ? 4 : 3;
-      for (int i = 0; i < 4; ++i) k.v[i] = i < nv ? (int64_t)EToV[e * 5 + kFaceVerts[f][i]] : INT64_MAX;
+      for (int i = 0; i < 4; ++i) {
+        if (i >= nv) {
+          k.v[i] = INT64_MAX;
+          continue;
+        }
+        const int64_t gv = EToV[e * 5 + kFaceVerts[f][i]];
+        k.v[i] = periodic ? canon[(size_t)gv] : gv;
+      }
       std::sort(k.v, k.v + 4);
       k.elem = e;
       k.face = f;
@@ -342,20 +389,10 @@ int build_connectivity(const double* V, int64_t Nv, const int32_t* EToV, int64_t
   int64_t boundary = 0;
   std::vector<double> X1((size_t)n2 * 3), X2((size_t)n2 * 3);
   double ev1[15], ev2[15];
-  size_t i = 0;
-  while (i < keys.size()) {
-    size_t j = i + 1;
-    while (j < keys.size() && keys[j].same(keys[i])) ++j;
-    if (j - i > 2) {
-      err = "a face is shared by more than two elements";
-      return -2;
-    }
-    if (j - i == 1) {
-      ++boundary;
-      i = j;
-      continue;
-    }
-    const FaceKey &A = keys[i], &B = keys[i + 1];
+  // Match the cubature points of faces A and B (coincident modulo the period on a
+  // periodic box) under one of the face's point symmetries; on success write both
+  // directions of mapP. Returns false if no symmetry makes the points coincide.
+  auto try_pair = [&](const FaceKey& A, const FaceKey& B) -> bool {
     for (int m = 0; m < 15; ++m) {
       ev1[m] = V[(int64_t)EToV[A.elem * 5 + m / 3] * 3 + m % 3];
       ev2[m] = V[(int64_t)EToV[B.elem * 5 + m / 3] * 3 + m % 3];
@@ -383,26 +420,64 @@ int build_connectivity(const double* V, int64_t Nv, const int32_t* EToV, int64_t
       bool ok = true;
       for (int idx = 0; idx < n2 && ok; ++idx) {
         const int jdx = permute(code, idx, n1);
-        for (int m = 0; m < 3; ++m)
-          if (std::fabs(X1[(size_t)idx * 3 + m] - X2[(size_t)jdx * 3 + m]) > tol) ok = false;
+        for (int m = 0; m < 3; ++m) {
+          double dx = X1[(size_t)idx * 3 + m] - X2[(size_t)jdx * 3 + m];
+          if (periodic) dx -= pL * std::nearbyint(dx / pL);  // equal modulo the period
+          if (std::fabs(dx) > tol) ok = false;
+        }
       }
       if (ok) found = code;
     }
-    if (found < 0) {
-      char buf[200];
-      std::snprintf(buf, sizeof buf,
-                    "face %d of element %lld and face %d of element %lld share vertices but not cubature "
-                    "points (non-conforming collapse)",
-                    A.face, (long long)A.elem, B.face, (long long)B.elem);
-      err = buf;
-      return -2;
-    }
+    if (found < 0) return false;
     for (int idx = 0; idx < n2; ++idx) {
       const int jdx = permute(found, idx, n1);
       const int64_t ga = A.elem * Nfc + (int64_t)A.face * n2 + idx;
       const int64_t gb = B.elem * Nfc + (int64_t)B.face * n2 + jdx;
       mapP[(size_t)ga] = gb;
       mapP[(size_t)gb] = ga;
+    }
+    return true;
+  };
+  size_t i = 0;
+  while (i < keys.size()) {
+    size_t j = i + 1;
+    while (j < keys.size() && keys[j].same(keys[i])) ++j;
+    const size_t cnt = j - i;
+    if (cnt > 2 && !periodic) {
+      err = "a face is shared by more than two elements";
+      return -2;
+    }
+    if (cnt == 1) {
+      ++boundary;
+      i = j;
+      continue;
+    }
+    if (cnt == 2) {
+      if (!try_pair(keys[i], keys[i + 1])) {
+        char buf[200];
+        std::snprintf(buf, sizeof buf,
+                      "face %d of element %lld and face %d of element %lld share vertices but not cubature "
+                      "points (non-conforming collapse)",
+                      keys[i].face, (long long)keys[i].elem, keys[i + 1].face, (long long)keys[i + 1].elem);
+        err = buf;
+        return -2;
+      }
+      i = j;
+      continue;
+    }
+    // Periodic box with two cells along an axis: distinct faces can share all vertices
+    // once opposite planes are identified; pair them by their cubature points.
+    std::vector<char> used(cnt, 0);
+    for (size_t a = 0; a < cnt; ++a) {
+      if (used[a]) continue;
+      for (size_t b2 = a + 1; b2 < cnt; ++b2) {
+        if (used[b2] || keys[i + a].elem == keys[i + b2].elem) continue;
+        if (try_pair(keys[i + a], keys[i + b2])) {
+          used[a] = used[b2] = 1;
+          break;
+        }
+      }
+      if (!used[a]) ++boundary;
     }
     i = j;
   }

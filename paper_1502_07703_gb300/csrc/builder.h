@@ -22,7 +22,10 @@ int build_tables(int N, RefTables& t);
 double jacobian_ab(const double* v15, double a, double b);
 double area_over_volume(const double* v15, const double* xg, const double* wg, int n1);
 // Returns 0, or -2 (bad mesh) with a message in err.
+// period_box: null, or {lo, hi} to make the box [lo, hi]^3 periodic (faces on
+// opposite boundary planes are matched as neighbours).
 int build_connectivity(const double* V, int64_t Nv, const int32_t* EToV, int64_t K, int N,
-                       std::vector<int64_t>& mapP, int64_t* nbnd, std::string& err);
+                       std::vector<int64_t>& mapP, int64_t* nbnd, std::string& err,
+                       const double* period_box = nullptr);
 
 }  // namespace pyrdg

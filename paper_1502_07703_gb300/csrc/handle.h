@@ -17,6 +17,11 @@ struct pyr_dg {
   int device = 0;
   cudaStream_t stream = nullptr;
   int N = 0, Np = 0, Nfc = 0, precision = 0, bc = 0;
+  int equation = PYR_DG_WAVE;  // PYR_DG_WAVE or PYR_DG_ADVECTION
+  int nf = 4;                  // fields per element in the state
+  double beta[3] = {1.0, 0.0, 0.0};
+  double box_lo = 0.0, box_hi = 1.0;
+  bool use_stage32 = false;    // FP32 wave handle: single-launch stage kernel
   double tau = 1.0;
   int64_t K = 0;
   size_t tsize = 8;

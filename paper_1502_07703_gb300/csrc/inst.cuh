@@ -2,6 +2,7 @@
 #pragma once
 #include "dg_kernels.cuh"
 #include "stage32.cuh"
+#include "adv_kernels.cuh"
 #include "launch.h"
 
 namespace pyrdg {
@@ -17,6 +18,7 @@ struct Impl {
   static_assert(ErrSmem<N>::bytes + 8 * (15 + 2 * 16) <= kMaxSmem, "error kernel shared memory");
   static_assert(4 * Dims<N>::n2 <= 4 * Dims<N>::n1 * Dims<N>::P3 * Dims<N>::P3, "projection B/J scratch");
   static_assert(S32<N>::bytes <= kMaxSmem, "FP32 stage kernel shared memory");
+  static_assert(Rhs1Smem<N, T>::bytes <= kMaxSmem && Proj1Smem<N>::bytes <= kMaxSmem, "advection shared memory");
 
   static cudaError_t prepare() {
     cudaError_t e = cudaFuncSetAttribute(trace_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -31,8 +33,54 @@ struct Impl {
     e = cudaFuncSetAttribute(project_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)ProjSmem<N>::bytes);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(trace1_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Trace1Smem<N, T>::bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(rhs1_kernel<N, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Rhs1Smem<N, T>::bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(rhs1_kernel<N, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Rhs1Smem<N, T>::bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(project1_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Proj1Smem<N>::bytes);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(error_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)ErrSmem<N>::bytes);
+  }
+  static AdvParams adv(const double* beta, double alpha, double lo, double L) {
+    AdvParams P;
+    P.beta[0] = beta[0];
+    P.beta[1] = beta[1];
+    P.beta[2] = beta[2];
+    P.alpha = alpha;
+    P.lo = lo;
+    P.L = L;
+    return P;
+  }
+  static void trace1(int64_t K, const void* q, const void* tab, void* tr, cudaStream_t s) {
+    trace1_kernel<N, T><<<(unsigned)K, NT, Trace1Smem<N, T>::bytes, s>>>(K, (const T*)q, (const T*)tab, (T*)tr);
+  }
+  static void rhs1(int64_t K, const void* qin, void* qout, void* res, const void* tr, const int32_t* mapP,
+                   const void* geo, const void* gface, const void* invM, const void* tab, const double* beta,
+                   double alpha, double rka, double rkb, double dt, int update, cudaStream_t s) {
+    if (update)
+      rhs1_kernel<N, T, true><<<(unsigned)K, NT, Rhs1Smem<N, T>::bytes, s>>>(
+          K, (const T*)qin, (T*)qout, (T*)res, (const T*)tr, mapP, (const T*)geo, (const T*)gface, (const T*)invM,
+          (const T*)tab, (T)beta[0], (T)beta[1], (T)beta[2], (T)alpha, (T)rka, (T)rkb, (T)dt);
+    else
+      rhs1_kernel<N, T, false><<<(unsigned)K, NT, Rhs1Smem<N, T>::bytes, s>>>(
+          K, (const T*)qin, (T*)qout, nullptr, (const T*)tr, mapP, (const T*)geo, (const T*)gface,
+          (const T*)invM, (const T*)tab, (T)beta[0], (T)beta[1], (T)beta[2], (T)alpha, (T)0, (T)0, (T)0);
+  }
+  static void project1(int64_t K, const double* ev, const double* gtab, const double* tabd, const double* beta,
+                       double lo, double L, double t, void* q, cudaStream_t s) {
+    project1_kernel<N, T><<<(unsigned)K, NT, Proj1Smem<N>::bytes, s>>>(K, ev, gtab, tabd, adv(beta, 0.0, lo, L), t,
+                                                                      (T*)q);
+  }
+  static void error1(int64_t K, const void* q, const double* ev, const double* gtab, const double* beta, double lo,
+                     double L, double t, double* partial, int nblocks, cudaStream_t s) {
+    error1_kernel<N, T><<<nblocks, 256, 0, s>>>(K, (const T*)q, ev, gtab, adv(beta, 0.0, lo, L), t, partial);
   }
   static void geom(int64_t K, const double* ev, const double* gtab, void* geo, void* gface, void* invM,
                    cudaStream_t s) {
@@ -118,6 +166,10 @@ struct Impl {
     l.rhs_out = &rhs_out;
     l.project = &project;
     l.error = &error;
+    l.trace1 = &trace1;
+    l.rhs1 = &rhs1;
+    l.project1 = &project1;
+    l.error1 = &error1;
     if (sizeof(T) == 4) {
       l.stage32 = &stage32;
       l.upload_c32 = &upload_c32;

@@ -33,6 +33,15 @@ struct Launchers {
   // Resident CTAs per SM of the FP32 stage kernel (for its persistent grid); 0 for double.
   int (*blocks_per_sm32)();
   size_t smem_stage32;
+  // Scalar advection (one field): trace, fused stage / rhs, projection and error norm.
+  void (*trace1)(int64_t K, const void* q, const void* tab, void* tr, cudaStream_t s);
+  void (*rhs1)(int64_t K, const void* qin, void* qout, void* res, const void* tr, const int32_t* mapP,
+               const void* geo, const void* gface, const void* invM, const void* tab, const double* beta,
+               double alpha, double rka, double rkb, double dt, int update, cudaStream_t s);
+  void (*project1)(int64_t K, const double* ev, const double* gtab, const double* tabd, const double* beta,
+                   double lo, double L, double t, void* q, cudaStream_t s);
+  void (*error1)(int64_t K, const void* q, const double* ev, const double* gtab, const double* beta, double lo,
+                 double L, double t, double* partial, int nblocks, cudaStream_t s);
 };
 
 // precision: 0 = double, 1 = float. Returns null for an unsupported degree.

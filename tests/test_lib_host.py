@@ -108,3 +108,24 @@ def test_raw_abi_null_and_range_checks():
     assert b"null" in L.pyr_dg_last_error()
     x = np.empty(4)
     assert L.pyr_dg_host_gauss_jacobi(0, 0.0, 0.0, x.ctypes.data_as(binding._c_dp), x.ctypes.data_as(binding._c_dp)) == -1
+
+
+def test_periodic_connectivity_matches_every_face():
+    N = 2
+    v, e = make_pyramid_mesh(3, 2, 2, delta=0.1, seed=8)
+    mapP, nb = binding.connectivity_periodic(v, e, N, box=(0.0, 1.0))
+    assert nb == 0
+    g = np.arange(mapP.size)
+    assert np.all(mapP[mapP] == g) and np.all(mapP != g)
+    n2 = (N + 1) ** 2
+    abc = np.array([_face_abc(N, f, i) for f in range(5) for i in range(n2)])
+    X, _ = map_points(v[e], *abc_to_rst(abc[:, 0], abc[:, 1], abc[:, 2]))
+    X = X.reshape(-1, 3)
+    d = np.mod(X[mapP] - X + 0.5, 1.0) - 0.5
+    assert np.max(np.abs(d)) < 1e-13
+
+
+def test_advection_setup_requires_periodic_box():
+    v, e = make_pyramid_mesh(1)
+    with pytest.raises(binding.PyrDGError, match="BAD_ARG"):
+        binding.Solver(v, e, 2, equation="advection")
