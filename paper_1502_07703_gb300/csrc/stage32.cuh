@@ -39,6 +39,15 @@ struct C32 {
 // upload_c32() from the double tables, rounded to float.
 static __constant__ float c32[C32<7>::size];
 
+// Ask L2 to fetch the 128-byte lines of [p, p + bytes) (one line per participating thread).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, int tid, int nthr) {
+  const char* c = reinterpret_cast<const char*>(p);
+  const size_t first = reinterpret_cast<size_t>(c) & ~size_t(127);
+  const size_t last = (reinterpret_cast<size_t>(c) + bytes - 1) & ~size_t(127);
+  for (size_t a = first + (size_t)tid * 128; a <= last; a += (size_t)nthr * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
 template <int N>
 struct S32 {
   using d = Dims<N>;
@@ -63,6 +72,9 @@ struct S32 {
   static constexpr size_t Z = A;                                 // 4 nrow YS [f][row][p'] (A, dA dead by then)
   // resident CTAs per SM the register budget is tuned for
   static constexpr int MIN_BLOCKS = N <= 5 ? 8 : 4;
+  // L2 prefetch of the next element: pays at N >= 6, where the per-element load latency
+  // is exposed longest; at lower N its registers push the kernel into spills
+  static constexpr bool PREFETCH = N >= 6;
   static constexpr size_t bytes = total * sizeof(float);
 };
 
@@ -107,6 +119,17 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
     }
     for (int x = tid; x < d::NGEO * n2; x += S::NT) s_geo[x] = geo[e * d::NGEO * n2 + x];
     for (int x = tid; x < d::NGF; x += S::NT) s_gf[x] = gface[e * d::NGF + x];
+    // the next element of this CTA: bring its contiguous inputs into L2 while this one computes
+    const int64_t en = e + gridDim.x;
+    if (S::PREFETCH && en < K) {
+      prefetch_l2(q + en * 4 * Np, sizeof(float) * 4 * Np, tid, S::NT);
+      prefetch_l2(res + en * 4 * Np, sizeof(float) * 4 * Np, tid, S::NT);
+      prefetch_l2(geo + en * d::NGEO * n2, sizeof(float) * d::NGEO * n2, tid, S::NT);
+      prefetch_l2(gface + en * d::NGF, sizeof(float) * d::NGF, tid, S::NT);
+      prefetch_l2(invM + en * Np, sizeof(float) * Np, tid, S::NT);
+      prefetch_l2(tr_cur + en * Nfc * 4, sizeof(float) * 4 * Nfc, tid, S::NT);
+      prefetch_l2(mapP + en * Nfc, sizeof(int32_t) * Nfc, tid, S::NT);
+    }
     __syncthreads();
 
     // ---- surface flux at every face point (a4), weighted by w sJ
@@ -153,6 +176,13 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
           s_A[o] = a;
           s_dA[o] = da;
         }
+      }
+    }
+    if (S::PREFETCH && e + gridDim.x < K) {  // neighbour traces of the next element (its mapP is in L2 by now)
+      const int64_t en = e + gridDim.x;
+      for (int g = tid; g < Nfc; g += S::NT) {
+        const float* pn = tr_cur + (int64_t)mapP[en * Nfc + g] * 4;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(pn));
       }
     }
     __syncthreads();
