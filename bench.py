@@ -432,10 +432,10 @@ def main():
     rhs_avg_s = rhs_ms / rhs_n * 1e-3
     achieved = rhs_flops_per_element(nd) * K / rhs_avg_s / 1e12
     # DRAM bytes per element of the fused stage kernel, from the ncu capture summarised in
-    # profiles/rhs_kernel_n4_f64_24cube.md (82,944 pyramids, N = 4, FP64: 1196.3 MB read +
+    # profiles/rhs_kernel_n4_f64_24cube.md (82,944 pyramids, N = 4, FP64: 1197.3 MB read +
     # write per launch); traffic scales with the element count. Valid for that kernel
     # version only: reset to None when the kernel changes, until it is measured again.
-    traffic = 14423.0 * K if (nd == 4 and prec == "f64" and args.nx >= 24) else None
+    traffic = 14435.0 * K if (nd == 4 and prec == "f64" and args.nx >= 24) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": f"rhs_kernel<{nd},{'double' if prec == 'f64' else 'float'},update>",
                 "peak_kind": f"{prec.upper()} FMA throughput measured in this run",
@@ -469,9 +469,11 @@ def main():
     forms = []
     if not args.no_forms:
         s.close()
-        for nx, delta, seed, n, prec, st in ((NX, DELTA, SEED, 4, "f32", 20), (NX, DELTA, SEED, 5, "f32", 20),
-                                             (NX, DELTA, SEED, 7, "f32", 10), (64, 0.1, 3, 5, "f32", 10)):
-            forms.append(measure_form(binding, nx, delta, seed, n, prec, st, 2, dev))
+        for f_nx, f_delta, f_seed, f_n, f_prec, f_st in ((NX, DELTA, SEED, 4, "f32", 20),
+                                                         (NX, DELTA, SEED, 5, "f32", 20),
+                                                         (NX, DELTA, SEED, 7, "f32", 10),
+                                                         (64, 0.1, 3, 5, "f32", 10)):
+            forms.append(measure_form(binding, f_nx, f_delta, f_seed, f_n, f_prec, f_st, 2, dev))
         forms.append(measure_batch(binding, 10, 2, dev))
         forms.append(measure_advection(binding, NX, 4, "f64", 10, 2, dev))
         forms.append(measure_advection(binding, NX, 4, "f32", 20, 2, dev))
