@@ -133,15 +133,6 @@ struct Impl {
       h[C::WFT + x] = (float)tab[L.WFT + x];
     }
     for (int k = 0; k <= N; ++k) h[C::GB + k] = (float)tab[L.GB + k];
-    for (int k = 0; k <= N; ++k)
-      for (int j = 0; j <= k; ++j) {
-        const int r = tri_num(k) + j;
-        for (int c = 0; c <= N; ++c) {
-          h[C::CB + r * d::n1 + c] = (float)(tab[L.GB + k] * tab[L.LX + r * d::P3 + c]);
-          h[C::CFm + r * d::n1 + c] = (float)(tab[L.GF + k * d::n1 + c] * tab[L.LX + r * d::P3 + d::n1]);
-          h[C::CFp + r * d::n1 + c] = (float)(tab[L.GF + k * d::n1 + c] * tab[L.LX + r * d::P3 + d::n1 + 1]);
-        }
-      }
     cudaError_t e = cudaMemcpyToSymbol(c32, h, sizeof(float) * C::size);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(stage32_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S32<N>::bytes);

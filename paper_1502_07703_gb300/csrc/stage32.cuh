@@ -3,14 +3,17 @@
 // Same arithmetic as rhs_kernel (sum-factorised volume term with the c direction
 // as level mixing, flux, lift, diagonal M^{-1}, LSRK update), organised for the
 // FP32 pipe, which retires 61x more FMAs per cycle than the FP64 pipe and so
-// exposes every extra instruction:
+// exposes every extra instruction and every exposed load latency:
 //  - reference tables live in constant memory and every loop over them is fully
 //    unrolled, so table operands are immediate constant-bank operands of FFMA;
 //  - each thread owns a column of one pass and keeps its data in registers;
+//    the work items of each pass are spread over all four warps;
+//  - CTAs are persistent (grid-stride over elements); while one element is
+//    computed, the next element's contiguous inputs (state, residual, geometry,
+//    M^{-1}) arrive in a second shared-memory buffer by cp.async;
 //  - the kernel also interpolates the updated state to the face points (the
 //    trace step of Alg. 3) into the other half of a ping-pong trace buffer, so
-//    a stage is a single launch and the state is read once;
-//  - CTAs are persistent (grid-stride over elements); tables are staged once.
+//    a stage is a single launch and the state is read once.
 #pragma once
 
 #include "dg_kernels.cuh"
@@ -29,10 +32,7 @@ struct C32 {
   static constexpr int GF = GB + d::n1;             // [k][m] G_k at GJ(1,0) point m
   static constexpr int WB = GF + d::n2;             // [p + n1 q] base-face weights
   static constexpr int WFT = WB + d::n2;            // [e + n1 m] triangle-face weights
-  static constexpr int CB = WFT + d::n2;            // [tri(k)+j][q] G_k(-1) l_j^k(b_q): base trace
-  static constexpr int CFm = CB + d::nrow * d::n1;  // [tri(k)+j][m] G_k(c_m) l_j^k(-1): face b = -1
-  static constexpr int CFp = CFm + d::nrow * d::n1; // [tri(k)+j][m] G_k(c_m) l_j^k(+1): face b = +1
-  static constexpr int size = CFp + d::nrow * d::n1;
+  static constexpr int size = WFT + d::n2;
 };
 
 // One copy per translation unit (each unit instantiates one degree); filled by
@@ -48,6 +48,15 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, int tid
     asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
 }
 
+__device__ __forceinline__ void cp_async16(void* s, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g));
+}
+__device__ __forceinline__ void cp_async4(void* s, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <int N>
 struct S32 {
   using d = Dims<N>;
@@ -59,21 +68,25 @@ struct S32 {
   static constexpr size_t al4(size_t x) { return (x + 3) / 4 * 4; }  // 16-byte alignment
   static constexpr size_t lx = 0;                                // LX copy (nrow x P3)
   static constexpr size_t dl = lx + d::nrow * d::P3;             // DL copy (nrow x n1)
-  static constexpr size_t u = al4(dl + d::nrow * d::n1);         // state (4 Np), old then new
-  static constexpr size_t geo = u + 4 * d::Np;                   // 9 n2
-  static constexpr size_t gf = geo + d::NGEO * d::n2;            // NGF
-  static constexpr size_t Fs = gf + d::NGF;                      // 4 Nfc  [f][g]
+  // inputs of one element, in two buffers (the next element's arrive by cp.async):
+  // state (4 Np; the new state replaces it), residual (4 Np), geometry (9 n2), face
+  // geometry (NGF), M^{-1} (Np); each part starts on a 16-byte boundary
+  static constexpr size_t bu = 0, bres = al4(4 * d::Np), bgeo = bres + al4(4 * d::Np),
+                          bgf = bgeo + al4(d::NGEO * d::n2), binv = bgf + al4(d::NGF), bsz = binv + al4(d::Np);
+  static constexpr size_t buf = al4(dl + d::nrow * d::n1);       // 2 x bsz
+  static constexpr size_t Fs = buf + 2 * bsz;                    // 4 Nfc  [f][g]
   static constexpr size_t A = Fs + 4 * d::Nfc;                   // [f][row][p]: a pass of u_old
   static constexpr size_t dA = A + 4 * d::nrow * d::n1;          // [f][row][p]: a pass, d/da
   static constexpr size_t ZA = 4 * d::nrow * YS > 8 * d::nrow * d::n1 ? 4 * d::nrow * YS : 8 * d::nrow * d::n1;
   static constexpr size_t Y = A + ZA;                            // 4 n1 nY  [f][k][p'][q']
-  static constexpr size_t Af = Y + 4 * d::n1 * nY;               // 4 x 2 x nrow: A at a = -1, +1 of u_new
-  static constexpr size_t total = Af + 8 * d::nrow;
+  static constexpr size_t total = Y + 4 * d::n1 * nY;
   static constexpr size_t Z = A;                                 // 4 nrow YS [f][row][p'] (A, dA dead by then)
+  static_assert(4 * d::nrow * d::P3 <= ZA, "trace a pass (At) aliases the A/dA region");
   // resident CTAs per SM the register budget is tuned for
   static constexpr int MIN_BLOCKS = N <= 5 ? 8 : 4;
-  // L2 prefetch of the next element: pays at N >= 6, where the per-element load latency
-  // is exposed longest; at lower N its registers push the kernel into spills
+  // L2 prefetch of the next element's own and neighbour traces and connectivity: used at
+  // N >= 6, where each element's flux gathers are longest; at lower N its registers push
+  // the kernel into spills
   static constexpr bool PREFETCH = N >= 6;
   static constexpr size_t bytes = total * sizeof(float);
 };
@@ -93,14 +106,10 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
   float* sm = reinterpret_cast<float*>(smem_raw);
   float* s_lx = sm + S::lx;
   float* s_dl = sm + S::dl;
-  float* s_u = sm + S::u;
-  float* s_geo = sm + S::geo;
-  float* s_gf = sm + S::gf;
   float* s_Fs = sm + S::Fs;
   float* s_A = sm + S::A;
   float* s_dA = sm + S::dA;
   float* s_Y = sm + S::Y;
-  float* s_Af = sm + S::Af;
   float* s_Z = sm + S::Z;
   const int tid = threadIdx.x;
 
@@ -109,28 +118,37 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
   // Y entries that no pass writes (face rows x face columns) stay zero
   for (int x = tid; x < 4 * n1 * nY; x += S::NT) s_Y[x] = 0.f;
 
-  for (int64_t e = blockIdx.x; e < K; e += gridDim.x) {
-    __syncthreads();
-    // ---- load the element
-    {
-      const float4* src = reinterpret_cast<const float4*>(q + e * 4 * Np);
-      float4* dst = reinterpret_cast<float4*>(s_u);
-      for (int x = tid; x < Np; x += S::NT) dst[x] = src[x];  // 4 Np floats = Np float4
+  // asynchronous copy of element en's contiguous inputs into buffer block bb. Each
+  // element's blocks start on 16-byte boundaries: 4 Np and NGF = 16 + 4 n2 floats are
+  // multiples of 4; geometry and M^{-1} go by 4-byte copies.
+  auto issue = [&](int64_t en, float* bb) {
+    for (int x = tid; x < Np; x += S::NT) {
+      cp_async16(bb + S::bu + 4 * x, q + en * 4 * Np + 4 * x);
+      cp_async16(bb + S::bres + 4 * x, res + en * 4 * Np + 4 * x);
     }
-    for (int x = tid; x < d::NGEO * n2; x += S::NT) s_geo[x] = geo[e * d::NGEO * n2 + x];
-    for (int x = tid; x < d::NGF; x += S::NT) s_gf[x] = gface[e * d::NGF + x];
-    // the next element of this CTA: bring its contiguous inputs into L2 while this one computes
+    for (int x = tid; x < d::NGEO * n2; x += S::NT) cp_async4(bb + S::bgeo + x, geo + en * d::NGEO * n2 + x);
+    for (int x = tid; x < d::NGF / 4; x += S::NT) cp_async16(bb + S::bgf + 4 * x, gface + en * d::NGF + 4 * x);
+    for (int x = tid; x < Np; x += S::NT) cp_async4(bb + S::binv + x, invM + en * Np + x);
+    cp_async_commit();
+  };
+  if ((int64_t)blockIdx.x < K) issue(blockIdx.x, sm + S::buf);
+  int it = 0;
+  for (int64_t e = blockIdx.x; e < K; e += gridDim.x, ++it) {
+    float* bcur = sm + S::buf + (it & 1) * S::bsz;
+    float* s_u = bcur + S::bu;
+    float* s_geo = bcur + S::bgeo;
+    float* s_gf = bcur + S::bgf;
+    const float* s_res = bcur + S::bres;
+    const float* s_inv = bcur + S::binv;
+    cp_async_wait_all();  // this thread's copies of element e have landed
+    __syncthreads();      // ... everyone's; and the other buffer's last reader is done
+    if (e + gridDim.x < K) issue(e + gridDim.x, sm + S::buf + ((it + 1) & 1) * S::bsz);
+    // the next element's traces and connectivity: into L2 while this one computes
     const int64_t en = e + gridDim.x;
     if (S::PREFETCH && en < K) {
-      prefetch_l2(q + en * 4 * Np, sizeof(float) * 4 * Np, tid, S::NT);
-      prefetch_l2(res + en * 4 * Np, sizeof(float) * 4 * Np, tid, S::NT);
-      prefetch_l2(geo + en * d::NGEO * n2, sizeof(float) * d::NGEO * n2, tid, S::NT);
-      prefetch_l2(gface + en * d::NGF, sizeof(float) * d::NGF, tid, S::NT);
-      prefetch_l2(invM + en * Np, sizeof(float) * Np, tid, S::NT);
       prefetch_l2(tr_cur + en * Nfc * 4, sizeof(float) * 4 * Nfc, tid, S::NT);
       prefetch_l2(mapP + en * Nfc, sizeof(int32_t) * Nfc, tid, S::NT);
     }
-    __syncthreads();
 
     // ---- surface flux at every face point (a4), weighted by w sJ
     for (int g = tid; g < Nfc; g += S::NT) {
@@ -187,73 +205,97 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
     }
     __syncthreads();
 
-    // ---- level mixing (c direction of Alg. 1) per (a,b) point, base lift; triangle-face c^T
-    for (int x = tid; x < n2 + 16 * n1; x += S::NT) {
-      if (x < n2) {
-        // b pass at this (a_p, b_q) point for all fields and levels, in registers
-        const int pq = x, p = pq % n1, qq = pq / n1;
+    // ---- level mixing (c direction of Alg. 1) per (a,b) point, base lift; triangle-face c^T.
+    // Two warp-aligned halves: the velocity half forms div(u) and feeds the p equation,
+    // the pressure half forms grad(p) and feeds the velocity equations.
+    constexpr int WV = (n2 + 31) / 32;
+    constexpr int MIXT = 2 * WV * 32;
+    static_assert(MIXT <= S::NT, "mixing slots");
+    if (tid < MIXT) {
+      const int half = tid / (WV * 32);
+      const int pq = tid - half * WV * 32;
+      if (pq < n2) {
+        const int p = pq % n1, qq = pq / n1;
         const float* g = s_geo + pq * d::NGEO;
-        float lq[nrow], dlq[nrow];
-#pragma unroll
-        for (int r = 0; r < nrow; ++r) {
-          lq[r] = s_lx[r * P3 + qq];
-          dlq[r] = s_dl[r * n1 + qq];
-        }
-        float U0[n1], Ua0[n1], Ub0[n1], X[n1], Zc[n1];
-#pragma unroll
-        for (int k = 0; k <= N; ++k) {
-          float u = 0.f, ua = 0.f, ub = 0.f;
-#pragma unroll
-          for (int j = 0; j <= k; ++j) {
-            const int o = (tri_num(k) + j) * n1 + p;
-            const float a = s_A[o], da = s_dA[o];
-            u = fmaf(a, lq[tri_num(k) + j], u);
-            ub = fmaf(a, dlq[tri_num(k) + j], ub);
-            ua = fmaf(da, lq[tri_num(k) + j], ua);
-          }
-          U0[k] = u;
-          Ua0[k] = ua;
-          Ub0[k] = ub;
-          float xs = 0.f, zs = 0.f;
-#pragma unroll
-          for (int m = 0; m < 3; ++m) {  // velocity fields: only the div combination is kept
-            float v = 0.f, va = 0.f, vb = 0.f;
-#pragma unroll
-            for (int j = 0; j <= k; ++j) {
-              const int o = ((m + 1) * nrow + tri_num(k) + j) * n1 + p;
-              const float a = s_A[o], da = s_dA[o];
-              v = fmaf(a, lq[tri_num(k) + j], v);
-              vb = fmaf(a, dlq[tri_num(k) + j], vb);
-              va = fmaf(da, lq[tri_num(k) + j], va);
-            }
-            xs = fmaf(g[m], va, fmaf(g[3 + m], vb, xs));
-            zs = fmaf(g[6 + m], v, zs);
-          }
-          X[k] = xs;
-          Zc[k] = zs;
-        }
-        float Fb[4];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) Fb[f] = s_Fs[f * Nfc + pq];
-#pragma unroll
-        for (int kp = 0; kp <= N; ++kp) {
-          float al = 0.f, be = 0.f, ga = 0.f, dv = 0.f;
+        if (half == 0) {
+          float X[n1], Zc[n1];
 #pragma unroll
           for (int k = 0; k <= N; ++k) {
-            const float mh = c32[C::MH + kp * n1 + k], mg = c32[C::MG + kp * n1 + k];
-            al = fmaf(mh, Ua0[k], al);
-            be = fmaf(mh, Ub0[k], be);
-            ga = fmaf(mg, U0[k], ga);
-            dv = fmaf(mh, X[k], fmaf(mg, Zc[k], dv));
-          }
-          const float gb = c32[C::GB + kp];
-          const int yo = kp * nY + p * YS + qq;
-          s_Y[0 * n1 * nY + yo] = fmaf(gb, Fb[0], dv);
+            float lq[n1], dlq[n1];
 #pragma unroll
-          for (int m = 0; m < 3; ++m)
-            s_Y[(m + 1) * n1 * nY + yo] = fmaf(gb, Fb[m + 1], fmaf(g[m], al, fmaf(g[3 + m], be, g[6 + m] * ga)));
+            for (int j = 0; j <= k; ++j) {
+              lq[j] = s_lx[(tri_num(k) + j) * P3 + qq];
+              dlq[j] = s_dl[(tri_num(k) + j) * n1 + qq];
+            }
+            float xs = 0.f, zs = 0.f;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+              float v = 0.f, va = 0.f, vb = 0.f;
+#pragma unroll
+              for (int j = 0; j <= k; ++j) {
+                const int o = ((m + 1) * nrow + tri_num(k) + j) * n1 + p;
+                const float a = s_A[o], da = s_dA[o];
+                v = fmaf(a, lq[j], v);
+                vb = fmaf(a, dlq[j], vb);
+                va = fmaf(da, lq[j], va);
+              }
+              xs = fmaf(g[m], va, fmaf(g[3 + m], vb, xs));
+              zs = fmaf(g[6 + m], v, zs);
+            }
+            X[k] = xs;
+            Zc[k] = zs;
+          }
+          const float Fb = s_Fs[pq];
+#pragma unroll
+          for (int kp = 0; kp <= N; ++kp) {
+            float dv = 0.f;
+#pragma unroll
+            for (int k = 0; k <= N; ++k)
+              dv = fmaf(c32[C::MH + kp * n1 + k], X[k], fmaf(c32[C::MG + kp * n1 + k], Zc[k], dv));
+            s_Y[kp * nY + p * YS + qq] = fmaf(c32[C::GB + kp], Fb, dv);
+          }
+        } else {
+          float U0[n1], Ua0[n1], Ub0[n1];
+#pragma unroll
+          for (int k = 0; k <= N; ++k) {
+            float u = 0.f, ua = 0.f, ub = 0.f;
+#pragma unroll
+            for (int j = 0; j <= k; ++j) {
+              const int o = (tri_num(k) + j) * n1 + p;
+              const float a = s_A[o], da = s_dA[o];
+              const float lq = s_lx[(tri_num(k) + j) * P3 + qq], dlq = s_dl[(tri_num(k) + j) * n1 + qq];
+              u = fmaf(a, lq, u);
+              ub = fmaf(a, dlq, ub);
+              ua = fmaf(da, lq, ua);
+            }
+            U0[k] = u;
+            Ua0[k] = ua;
+            Ub0[k] = ub;
+          }
+          float Fb[3];
+#pragma unroll
+          for (int m = 0; m < 3; ++m) Fb[m] = s_Fs[(m + 1) * Nfc + pq];
+#pragma unroll
+          for (int kp = 0; kp <= N; ++kp) {
+            float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+            for (int k = 0; k <= N; ++k) {
+              const float mh = c32[C::MH + kp * n1 + k], mg = c32[C::MG + kp * n1 + k];
+              al = fmaf(mh, Ua0[k], al);
+              be = fmaf(mh, Ub0[k], be);
+              ga = fmaf(mg, U0[k], ga);
+            }
+            const float gb = c32[C::GB + kp];
+            const int yo = kp * nY + p * YS + qq;
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+              s_Y[(m + 1) * n1 * nY + yo] = fmaf(gb, Fb[m], fmaf(g[m], al, fmaf(g[3 + m], be, g[6 + m] * ga)));
+          }
         }
-      } else {
+      }
+    }
+    for (int x = ((tid + S::NT - MIXT) % S::NT) + n2; x < n2 + 16 * n1; x += S::NT) {
+      {
         const int y = x - n2;
         const int ee = y % n1;
         const int slot = (y / n1) % 4;
@@ -310,10 +352,10 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
       float acc = 0.f;
 #pragma unroll
       for (int c = 0; c < P3; ++c) acc = fmaf(lr[c], Zr[c], acc);
-      const float rhs = -invM[e * Np + n] * acc;
+      const float rhs = -s_inv[n] * acc;
       const int64_t gi = e * 4 * Np + x;
       const float dte = dt_elem ? dt_elem[e] : dt;  // per-element step when meshes are batched
-      const float rnew = fmaf(rka, res[gi], dte * rhs);
+      const float rnew = fmaf(rka, s_res[x], dte * rhs);
       res[gi] = rnew;
       const float unew = fmaf(rkb, rnew, s_u[x]);
       q[gi] = unew;
@@ -322,62 +364,82 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
     if (!write_traces) continue;
     __syncthreads();
 
-    // ---- traces of the updated state (Alg. 3's interpolation to face points) into tr_nxt
-    if (tid < 4 * P3) {
-      const int f = tid / P3, pp = tid - f * P3;
+    // ---- traces of the updated state (Alg. 3's interpolation to face points) into tr_nxt.
+    // First the a direction at every a point and a = -1, +1, by level groups:
+    // At[f][row(k,j)][pp] = sum_i u[f][k,j,i] l_i^k(a_pp)   (aliases the dead A/dA/Z region)
+    float* s_At = s_A;
+    for (int x = tid; x < S::G * 4 * P3; x += S::NT) {
+      const int grp = x / (4 * P3), y = x - grp * 4 * P3;
+      const int f = y / P3, pp = y - f * P3;
       const float* uf = s_u + f * Np;
-      float A[nrow];
 #pragma unroll
       for (int k = 0; k <= N; ++k) {
+        if (k != grp && k != N - grp) continue;
+        float lxc[n1];
+#pragma unroll
+        for (int i = 0; i <= k; ++i) lxc[i] = s_lx[(tri_num(k) + i) * P3 + pp];
 #pragma unroll
         for (int j = 0; j <= k; ++j) {
           float a = 0.f;
 #pragma unroll
-          for (int i = 0; i <= k; ++i)
-            a = fmaf(uf[lvl_off(k) + j * (k + 1) + i], s_lx[(tri_num(k) + i) * P3 + pp], a);
-          A[tri_num(k) + j] = a;
+          for (int i = 0; i <= k; ++i) a = fmaf(uf[lvl_off(k) + j * (k + 1) + i], lxc[i], a);
+          s_At[(f * nrow + tri_num(k) + j) * P3 + pp] = a;
         }
-      }
-      float* dst = tr_nxt + e * Nfc * 4 + f;
-      if (pp <= N) {
-#pragma unroll
-        for (int c = 0; c <= N; ++c) {
-          float tb = 0.f, tm = 0.f, tp = 0.f;
-#pragma unroll
-          for (int r = 0; r < nrow; ++r) {
-            tb = fmaf(c32[C::CB + r * n1 + c], A[r], tb);
-            tm = fmaf(c32[C::CFm + r * n1 + c], A[r], tm);
-            tp = fmaf(c32[C::CFp + r * n1 + c], A[r], tp);
-          }
-          dst[4 * (pp + n1 * c)] = tb;               // base point (a_pp, b_c)
-          dst[4 * (1 * n2 + pp + n1 * c)] = tm;      // face b = -1 at (a_pp, c_c)
-          dst[4 * (3 * n2 + pp + n1 * c)] = tp;      // face b = +1
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < nrow; ++r) s_Af[(f * 2 + (pp - n1)) * nrow + r] = A[r];
       }
     }
     __syncthreads();
-    if (tid < 8 * n1) {  // faces a = -1 (face 4) and a = +1 (face 2) at (b_e, c_m)
-      const int ee = tid % n1, side = (tid / n1) % 2, f = tid / (2 * n1);
-      const float* Af = s_Af + (f * 2 + side) * nrow;
-      float t[nrow];
+    // then the face points: 16 n1 items for the four triangular faces (a level sum,
+    // then the c direction), 4 n2 items for the base
+    {
+      float* dst = tr_nxt + e * Nfc * 4;
+      for (int x = tid; x < 16 * n1 + 4 * n2; x += S::NT) {
+        if (x < 16 * n1) {
+          const int f = x & 3, y = x >> 2;
+          const int t = y % n1, kind = y / n1;  // kind: 0 b=-1, 1 b=+1, 2 a=-1, 3 a=+1
+          // faces b = -1, +1 at (a_t, c_m): weights l_j^k(-1 or +1), A column t;
+          // faces a = -1, +1 at (b_t, c_m): weights l_j^k(b_t), A column a = -1 or +1
+          const int wcol = kind < 2 ? n1 + (kind & 1) : t;
+          const int acol = kind < 2 ? t : n1 + (kind & 1);
+          const float* Ar = s_At + f * nrow * P3 + acol;
+          const float* wr = s_lx + wcol;
+          float Sk[n1];
 #pragma unroll
-      for (int r = 0; r < nrow; ++r) t[r] = Af[r] * s_lx[r * P3 + ee];
-      float* dst = tr_nxt + e * Nfc * 4 + f;
-      const int face = side == 0 ? 4 : 2;
+          for (int k = 0; k <= N; ++k) {
+            float sacc = 0.f;
 #pragma unroll
-      for (int m = 0; m <= N; ++m) {
-        float acc = 0.f;
+            for (int j = 0; j <= k; ++j) {
+              const int r = tri_num(k) + j;
+              sacc = fmaf(wr[r * P3], Ar[r * P3], sacc);
+            }
+            Sk[k] = sacc;
+          }
+          const int face = kind == 0 ? 1 : kind == 1 ? 3 : kind == 2 ? 4 : 2;
 #pragma unroll
-        for (int k = 0; k <= N; ++k) {
-          float s = 0.f;
+          for (int m = 0; m <= N; ++m) {
+            float acc = 0.f;
 #pragma unroll
-          for (int j = 0; j <= k; ++j) s += t[tri_num(k) + j];
-          acc = fmaf(c32[C::GF + k * n1 + m], s, acc);
+            for (int k = 0; k <= N; ++k) acc = fmaf(c32[C::GF + k * n1 + m], Sk[k], acc);
+            dst[4 * (face * n2 + t + n1 * m) + f] = acc;
+          }
+        } else {  // base (c = -1) at (a_t, b_c)
+          const int y = x - 16 * n1;
+          const int f = y & 3, z = y >> 2;
+          const int t = z % n1, c = z / n1;
+          const float* Ar = s_At + f * nrow * P3 + t;
+          const float* wr = s_lx + c;
+          float acc = 0.f;
+#pragma unroll
+          for (int k = 0; k <= N; ++k) {
+            float sacc = 0.f;
+#pragma unroll
+            for (int j = 0; j <= k; ++j) {
+              const int r = tri_num(k) + j;
+              sacc = fmaf(wr[r * P3], Ar[r * P3], sacc);
+            }
+            acc = fmaf(c32[C::GB + k], sacc, acc);
+          }
+          dst[4 * (t + n1 * c) + f] = acc;
         }
-        dst[4 * (face * n2 + ee + n1 * m)] = acc;
       }
     }
   }
