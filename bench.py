@@ -52,16 +52,20 @@ def rhs_flops_per_element(n):
 
     Counts a multiply-add as 2 flops, following the kernel's passes: a pass
     (A, dA), b pass (U, U_a, U_b), per-level combination of the three velocity
-    fields for div(u), level mixing of the c direction (MH, MG) with the chain
-    rule and the base-face lift, triangle-face c^T pass, b^T and a^T passes,
-    face flux, M^{-1} and the LSRK update."""
+    fields for div(u), level mixing of the c direction (MH tridiagonal, MG lower
+    Hessenberg: only their nonzero entries) with the chain rule and the base-face
+    lift, triangle-face c^T pass, b^T and a^T passes, face flux, M^{-1} and the
+    LSRK update."""
     n1, n2, P3 = n + 1, (n + 1) ** 2, n + 3
     Np, nrow, Nfc = num_modes(n), n1 * (n1 + 1) // 2, 5 * n2
     sum_k1 = n1 * (n1 + 1) // 2  # sum_k (k+1)
+    nnz_h = 3 * n1 - 2                                  # tridiagonal MH
+    nnz_g = sum(min(kp + 2, n1) for kp in range(n1))    # lower Hessenberg MG
     mac = 4 * n1 * 2 * Np                       # a pass: 2 outputs, (k+1) terms, per (f, k, j, p)
     mac += 4 * n2 * 3 * sum_k1                  # b pass: 3 outputs per (f, k, pq), (k+1) terms
     mac += n1 * n2 * 9                          # div combination per (k, pq)
-    mac += n1 * n2 * (5 * n1 + 13)              # level mixing + chain rule + base lift per (k', pq)
+    mac += n2 * (3 * nnz_h + 2 * nnz_g)         # level mixing: al, be, div(u)_r,s with MH; ga, div(u)_c with MG
+    mac += n1 * n2 * 13                         # chain rule + base lift per (k', pq)
     mac += 16 * n1 * n1 * n1                    # triangle-face c^T
     mac += 4 * nrow * (n1 * P3 + 2 * n1)        # b^T pass
     mac += 4 * Np * P3                          # a^T pass
@@ -431,11 +435,9 @@ def main():
     peak = binding.fma_peak(prec)
     rhs_avg_s = rhs_ms / rhs_n * 1e-3
     achieved = rhs_flops_per_element(nd) * K / rhs_avg_s / 1e12
-    # DRAM bytes per element of the fused stage kernel, from the ncu capture summarised in
-    # profiles/rhs_kernel_n4_f64_24cube.md (82,944 pyramids, N = 4, FP64: 1197.3 MB read +
-    # write per launch); traffic scales with the element count. Valid for that kernel
-    # version only: reset to None when the kernel changes, until it is measured again.
-    traffic = 14435.0 * K if (nd == 4 and prec == "f64" and args.nx >= 24) else None
+    # DRAM bytes per launch of the fused stage kernel from an ncu capture of this kernel
+    # version (scaled by the element count); None until one is taken.
+    traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": f"rhs_kernel<{nd},{'double' if prec == 'f64' else 'float'},update>",
                 "peak_kind": f"{prec.upper()} FMA throughput measured in this run",

@@ -209,10 +209,12 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
       const T* mh = s_tab + L.MH + kp * d::n1;
       const T* mg = s_tab + L.MG + kp * d::n1;
       T al = 0, be = 0, ga = 0;
-      for (int k = 0; k <= N; ++k) {
+      // MG is lower Hessenberg (k <= k'+1), MH tridiagonal (|k - k'| <= 1)
+      const int k1 = kp < N ? kp + 1 : N;
+      for (int k = 0; k <= k1; ++k) ga += mg[k] * s_U[k * d::n2 + pq];
+      for (int k = kp > 0 ? kp - 1 : 0; k <= k1; ++k) {
         al += mh[k] * s_Ua[k * d::n2 + pq];
         be += mh[k] * s_Ub[k * d::n2 + pq];
-        ga += mg[k] * s_U[k * d::n2 + pq];
       }
       const T* g = s_geo + pq * d::NGEO;
       const T b1 = bx * g[0] + by * g[1] + bz * g[2];

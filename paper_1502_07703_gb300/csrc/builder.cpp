@@ -164,6 +164,15 @@ int build_tables(int N, RefTables& t) {
   for (int r = 0; r < n1; ++r) t.tab[L.WC + r] = 0.25 * wc[r];
   // The volume geometric factors do not depend on c, so the c-interpolation of
   // derivatives and the c-projection onto level k' collapse into these sums.
+  // Both are banded. With G_k = ((1-c)/2)^k P_{N-k}^{(2k+3,0)}, the integrand of
+  // MH[k'][k] is (1-c)^{k+k'+1} P_{N-k'} P_{N-k} (up to a constant), symmetric in k, k';
+  // for k >= k'+2 it is (1-c)^{2k'+3} times a polynomial of degree N-k'-2, which
+  // P_{N-k'}^{(2k'+3,0)} is orthogonal to. So MH is tridiagonal. G_k' carries
+  // ((1-c)/2)^{k-1}, so MG[k'][k] vanishes for k >= k'+2 by the same argument (lower
+  // Hessenberg). The GJ(2,0) rule is exact on these entries (polynomials of degree
+  // 2N-1), so the sums are zero up to rounding; they are stored as exact zeros and
+  // the kernels skip them.
+  double mmax = 0.0, resid = 0.0;
   for (int kp = 0; kp <= N; ++kp)
     for (int k = 0; k <= N; ++k) {
       double mh = 0.0, mg = 0.0;
@@ -172,9 +181,19 @@ int build_tables(int N, RefTables& t) {
         mh += w * t.tab[L.HC + k * n1 + r];
         mg += w * t.tab[L.DGC + k * n1 + r];
       }
+      mmax = std::max(mmax, std::max(std::fabs(mh), std::fabs(mg)));
+      if (k > kp + 1 || k < kp - 1) {
+        resid = std::max(resid, std::fabs(mh));
+        mh = 0.0;
+      }
+      if (k > kp + 1) {
+        resid = std::max(resid, std::fabs(mg));
+        mg = 0.0;
+      }
       t.tab[L.MH + kp * n1 + k] = mh;
       t.tab[L.MG + kp * n1 + k] = mg;
     }
+  if (resid > 1e-12 * mmax) return -3;  // the band structure must hold to rounding
   for (int q = 0; q < n1; ++q)
     for (int p = 0; p < n1; ++p) {
       t.tab[L.WB + p + n1 * q] = wg[p] * wg[q];

@@ -201,7 +201,10 @@ __global__ void __launch_bounds__(KCfg<N>::NT) trace_kernel(int64_t K, const T* 
     const T* uc = s_u + f * d::Np + lvl_off(k) + j * (k + 1);
     const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + pp;
     T acc = 0;
-    for (int i = 0; i <= k; ++i) acc += uc[i] * lx[i * d::P3];
+    if (k == N && pp < d::n1)  // the level-N nodes are the volume-rule points: l_i^N(x_p) = delta_ip
+      acc = uc[pp];
+    else
+      for (int i = 0; i <= k; ++i) acc += uc[i] * lx[i * d::P3];
     s_A[(f * d::nrow + tri_num(k) + j) * d::P3 + pp] = acc;
   }
   __syncthreads();
@@ -228,7 +231,10 @@ __global__ void __launch_bounds__(KCfg<N>::NT) trace_kernel(int64_t K, const T* 
     const T* Ar = s_A + (f * d::nrow + tri_num(k)) * d::P3 + pa;
     const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + qb;
     T acc = 0;
-    for (int j = 0; j <= k; ++j) acc += Ar[j * d::P3] * lx[j * d::P3];
+    if (k == N && qb < d::n1)  // l_j^N(b_q) = delta_jq
+      acc = Ar[qb * d::P3];
+    else
+      for (int j = 0; j <= k; ++j) acc += Ar[j * d::P3] * lx[j * d::P3];
     s_B[(f * d::n1 + k) * S::nB + s] = acc;
   }
   __syncthreads();
@@ -442,9 +448,14 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
     const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + p;
     const T* dl = s_tab + L.DL + tri_num(k) * d::n1 + p;
     T a = 0, da = 0;
-    for (int i = 0; i <= k; ++i) {
-      a += uc[i] * lx[i * d::P3];
-      da += uc[i] * dl[i * d::n1];
+    if (k == N) {  // the level-N nodes are the volume-rule points: l_i^N(a_p) = delta_ip
+      a = uc[p];
+      for (int i = 0; i <= k; ++i) da += uc[i] * dl[i * d::n1];
+    } else {
+      for (int i = 0; i <= k; ++i) {
+        a += uc[i] * lx[i * d::P3];
+        da += uc[i] * dl[i * d::n1];
+      }
     }
     const int o = (f * d::nrow + tri_num(k) + j) * d::n1 + p;
     s_A[o] = a;
@@ -462,11 +473,17 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
     const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + q;
     const T* dl = s_tab + L.DL + tri_num(k) * d::n1 + q;
     T u = 0, ua = 0, ub = 0;
-    for (int j = 0; j <= k; ++j) {
-      const T av = Ar[j * d::n1], lv = lx[j * d::P3];
-      u += av * lv;
-      ub += av * dl[j * d::n1];
-      ua += dAr[j * d::n1] * lv;
+    if (k == N) {  // l_j^N(b_q) = delta_jq
+      u = Ar[q * d::n1];
+      ua = dAr[q * d::n1];
+      for (int j = 0; j <= k; ++j) ub += Ar[j * d::n1] * dl[j * d::n1];
+    } else {
+      for (int j = 0; j <= k; ++j) {
+        const T av = Ar[j * d::n1], lv = lx[j * d::P3];
+        u += av * lv;
+        ub += av * dl[j * d::n1];
+        ua += dAr[j * d::n1] * lv;
+      }
     }
     const int o = (f * d::n1 + k) * d::n2 + pq;
     s_U[o] = u;
@@ -501,13 +518,18 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
       const T* mh = s_tab + L.MH + kp * d::n1;
       const T* mg = s_tab + L.MG + kp * d::n1;
       T al = 0, be = 0, ga = 0, dv = 0;
-#pragma unroll
-      for (int k = 0; k <= N; ++k) {
+      // MG is lower Hessenberg (k <= k'+1), MH tridiagonal (|k - k'| <= 1)
+      const int k1 = kp < N ? kp + 1 : N;
+      for (int k = 0; k <= k1; ++k) {
         const int o = k * d::n2 + pq;  // field 0 (p)
+        ga += mg[k] * s_U[o];
+        dv += mg[k] * s_Zc[o];
+      }
+      for (int k = kp > 0 ? kp - 1 : 0; k <= k1; ++k) {
+        const int o = k * d::n2 + pq;
         al += mh[k] * s_Ua[o];
         be += mh[k] * s_Ub[o];
-        ga += mg[k] * s_U[o];
-        dv += mh[k] * s_X[o] + mg[k] * s_Zc[o];
+        dv += mh[k] * s_X[o];
       }
       const T* g = s_geo + pq * d::NGEO;
       const T gb = s_tab[L.GB + kp];
@@ -559,7 +581,12 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
     const T* Yr = s_Y + ((f * d::n1 + k) * d::P3 + pp) * d::P3;
     const T* lx = s_tab + L.LX + (tri_num(k) + j) * d::P3;
     T acc = 0;
-    for (int q = 0; q < nq; ++q) acc += lx[q] * Yr[q];
+    if (k == N) {  // l_j^N(x_q) = delta_jq on the volume points; the face columns remain
+      acc = Yr[j];
+      for (int q = d::n1; q < nq; ++q) acc += lx[q] * Yr[q];
+    } else {
+      for (int q = 0; q < nq; ++q) acc += lx[q] * Yr[q];
+    }
     s_Zb[(f * d::nrow + row) * d::P3 + pp] = acc;
   }
   __syncthreads();
@@ -571,8 +598,12 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
     const T* lx = s_tab + L.LX + (tri_num(k) + i) * d::P3;
     const T* Zr = s_Zb + (f * d::nrow + tri_num(k) + j) * d::P3;
     T acc = 0;
+    if (k == N) {  // l_i^N(x_p') = delta_ip' on the volume points; the face columns remain
+      acc = Zr[i] + lx[d::n1] * Zr[d::n1] + lx[d::n1 + 1] * Zr[d::n1 + 1];
+    } else {
 #pragma unroll
-    for (int pp = 0; pp < d::P3; ++pp) acc += lx[pp] * Zr[pp];
+      for (int pp = 0; pp < d::P3; ++pp) acc += lx[pp] * Zr[pp];
+    }
     const T rhs = -invM[e * d::Np + n] * acc;
     const int64_t gi = e * 4 * d::Np + x;
     if (UPDATE) {

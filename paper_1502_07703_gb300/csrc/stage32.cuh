@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
         float lxc[n1], dlc[n1];
 #pragma unroll
         for (int i = 0; i <= k; ++i) {
-          lxc[i] = s_lx[(tri_num(k) + i) * P3 + p];
+          if (k < N) lxc[i] = s_lx[(tri_num(k) + i) * P3 + p];
           dlc[i] = s_dl[(tri_num(k) + i) * n1 + p];
         }
 #pragma unroll
@@ -187,9 +187,11 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
 #pragma unroll
           for (int i = 0; i <= k; ++i) {
             const float c = uf[lvl_off(k) + j * (k + 1) + i];
-            a = fmaf(c, lxc[i], a);
+            if (k < N) a = fmaf(c, lxc[i], a);
             da = fmaf(c, dlc[i], da);
           }
+          // the level-N nodes are the volume-rule points: l_i^N(a_p) = delta_ip
+          if (k == N) a = uf[lvl_off(k) + j * (k + 1) + p];
           const int o = (f * nrow + tri_num(k) + j) * n1 + p;
           s_A[o] = a;
           s_dA[o] = da;
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
             float lq[n1], dlq[n1];
 #pragma unroll
             for (int j = 0; j <= k; ++j) {
-              lq[j] = s_lx[(tri_num(k) + j) * P3 + qq];
+              if (k < N) lq[j] = s_lx[(tri_num(k) + j) * P3 + qq];
               dlq[j] = s_dl[(tri_num(k) + j) * n1 + qq];
             }
             float xs = 0.f, zs = 0.f;
@@ -234,10 +236,17 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
 #pragma unroll
               for (int j = 0; j <= k; ++j) {
                 const int o = ((m + 1) * nrow + tri_num(k) + j) * n1 + p;
-                const float a = s_A[o], da = s_dA[o];
-                v = fmaf(a, lq[j], v);
+                const float a = s_A[o];
                 vb = fmaf(a, dlq[j], vb);
-                va = fmaf(da, lq[j], va);
+                if (k < N) {
+                  v = fmaf(a, lq[j], v);
+                  va = fmaf(s_dA[o], lq[j], va);
+                }
+              }
+              if (k == N) {  // l_j^N(b_q) = delta_jq
+                const int o = ((m + 1) * nrow + tri_num(k) + qq) * n1 + p;
+                v = s_A[o];
+                va = s_dA[o];
               }
               xs = fmaf(g[m], va, fmaf(g[3 + m], vb, xs));
               zs = fmaf(g[6 + m], v, zs);
@@ -250,8 +259,11 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
           for (int kp = 0; kp <= N; ++kp) {
             float dv = 0.f;
 #pragma unroll
-            for (int k = 0; k <= N; ++k)
-              dv = fmaf(c32[C::MH + kp * n1 + k], X[k], fmaf(c32[C::MG + kp * n1 + k], Zc[k], dv));
+            for (int k = 0; k <= N; ++k) {  // MG lower Hessenberg, MH tridiagonal
+              if (k > kp + 1) continue;
+              dv = fmaf(c32[C::MG + kp * n1 + k], Zc[k], dv);
+              if (k >= kp - 1) dv = fmaf(c32[C::MH + kp * n1 + k], X[k], dv);
+            }
             s_Y[kp * nY + p * YS + qq] = fmaf(c32[C::GB + kp], Fb, dv);
           }
         } else {
@@ -262,11 +274,18 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
 #pragma unroll
             for (int j = 0; j <= k; ++j) {
               const int o = (tri_num(k) + j) * n1 + p;
-              const float a = s_A[o], da = s_dA[o];
-              const float lq = s_lx[(tri_num(k) + j) * P3 + qq], dlq = s_dl[(tri_num(k) + j) * n1 + qq];
-              u = fmaf(a, lq, u);
-              ub = fmaf(a, dlq, ub);
-              ua = fmaf(da, lq, ua);
+              const float a = s_A[o];
+              ub = fmaf(a, s_dl[(tri_num(k) + j) * n1 + qq], ub);
+              if (k < N) {
+                const float lq = s_lx[(tri_num(k) + j) * P3 + qq];
+                u = fmaf(a, lq, u);
+                ua = fmaf(s_dA[o], lq, ua);
+              }
+            }
+            if (k == N) {  // l_j^N(b_q) = delta_jq
+              const int o = (tri_num(k) + qq) * n1 + p;
+              u = s_A[o];
+              ua = s_dA[o];
             }
             U0[k] = u;
             Ua0[k] = ua;
@@ -279,11 +298,12 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
           for (int kp = 0; kp <= N; ++kp) {
             float al = 0.f, be = 0.f, ga = 0.f;
 #pragma unroll
-            for (int k = 0; k <= N; ++k) {
-              const float mh = c32[C::MH + kp * n1 + k], mg = c32[C::MG + kp * n1 + k];
-              al = fmaf(mh, Ua0[k], al);
-              be = fmaf(mh, Ub0[k], be);
-              ga = fmaf(mg, U0[k], ga);
+            for (int k = 0; k <= N; ++k) {  // MG lower Hessenberg, MH tridiagonal
+              if (k > kp + 1) continue;
+              ga = fmaf(c32[C::MG + kp * n1 + k], U0[k], ga);
+              if (k < kp - 1) continue;
+              al = fmaf(c32[C::MH + kp * n1 + k], Ua0[k], al);
+              be = fmaf(c32[C::MH + kp * n1 + k], Ub0[k], be);
             }
             const float gb = c32[C::GB + kp];
             const int yo = kp * nY + p * YS + qq;
@@ -335,7 +355,13 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
         for (int j = 0; j <= k; ++j) {
           float acc = 0.f;
 #pragma unroll
-          for (int c = 0; c < P3; ++c) acc = fmaf(c32[C::LX + (tri_num(k) + j) * P3 + c], yv[c], acc);
+          for (int c = 0; c < P3; ++c) {
+            if (k == N && c < n1) {  // l_j^N(x_c) = delta_jc on the volume points
+              if (c == j) acc = yv[c];
+              continue;
+            }
+            acc = fmaf(c32[C::LX + (tri_num(k) + j) * P3 + c], yv[c], acc);
+          }
           s_Z[(f * nrow + tri_num(k) + j) * YS + pp] = acc;
         }
       }
@@ -350,8 +376,12 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
       const float* Zr = s_Z + (f * nrow + tri_num(k) + j) * YS;
       const float* lr = s_lx + (tri_num(k) + i) * P3;
       float acc = 0.f;
+      if (k == N) {  // l_i^N(x_c) = delta_ic on the volume points; the face columns remain
+        acc = fmaf(lr[n1 + 1], Zr[n1 + 1], fmaf(lr[n1], Zr[n1], Zr[i]));
+      } else {
 #pragma unroll
-      for (int c = 0; c < P3; ++c) acc = fmaf(lr[c], Zr[c], acc);
+        for (int c = 0; c < P3; ++c) acc = fmaf(lr[c], Zr[c], acc);
+      }
       const float rhs = -s_inv[n] * acc;
       const int64_t gi = e * 4 * Np + x;
       const float dte = dt_elem ? dt_elem[e] : dt;  // per-element step when meshes are batched
@@ -375,6 +405,7 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
 #pragma unroll
       for (int k = 0; k <= N; ++k) {
         if (k != grp && k != N - grp) continue;
+        if (k == N && pp < n1) continue;  // At[f][N,j][pp] = u[f][N,j,pp]: read from u below
         float lxc[n1];
 #pragma unroll
         for (int i = 0; i <= k; ++i) lxc[i] = s_lx[(tri_num(k) + i) * P3 + pp];
@@ -402,6 +433,9 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
           const int acol = kind < 2 ? t : n1 + (kind & 1);
           const float* Ar = s_At + f * nrow * P3 + acol;
           const float* wr = s_lx + wcol;
+          // level N at a volume column t: At is the state itself
+          const float* ArN = kind < 2 ? s_u + f * Np + lvl_off(N) + t : Ar + tri_num(N) * P3;
+          const int sN = kind < 2 ? n1 : P3;
           float Sk[n1];
 #pragma unroll
           for (int k = 0; k <= N; ++k) {
@@ -409,7 +443,7 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
 #pragma unroll
             for (int j = 0; j <= k; ++j) {
               const int r = tri_num(k) + j;
-              sacc = fmaf(wr[r * P3], Ar[r * P3], sacc);
+              sacc = fmaf(wr[r * P3], k == N ? ArN[j * sN] : Ar[r * P3], sacc);
             }
             Sk[k] = sacc;
           }
@@ -431,10 +465,14 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
 #pragma unroll
           for (int k = 0; k <= N; ++k) {
             float sacc = 0.f;
+            if (k == N) {  // l_j^N(b_c) = delta_jc and At[N][pp < n1] is u
+              sacc = s_u[f * Np + lvl_off(N) + c * n1 + t];
+            } else {
 #pragma unroll
-            for (int j = 0; j <= k; ++j) {
-              const int r = tri_num(k) + j;
-              sacc = fmaf(wr[r * P3], Ar[r * P3], sacc);
+              for (int j = 0; j <= k; ++j) {
+                const int r = tri_num(k) + j;
+                sacc = fmaf(wr[r * P3], Ar[r * P3], sacc);
+              }
             }
             acc = fmaf(c32[C::GB + k], sacc, acc);
           }
