@@ -48,35 +48,43 @@ def num_modes(n):
 
 
 def rhs_flops_per_element(n):
-    """Algorithmic FP64 flops of the fused stage kernel per element (sum-factorised).
+    """Algorithmic flops of the fused stage kernel per element (sum-factorised).
 
     Counts a multiply-add as 2 flops, following the kernel's passes: a pass
     (A, dA), b pass (U, U_a, U_b), per-level combination of the three velocity
     fields for div(u), level mixing of the c direction (MH tridiagonal, MG lower
     Hessenberg: only their nonzero entries) with the chain rule and the base-face
     lift, triangle-face c^T pass, b^T and a^T passes, face flux, M^{-1} and the
-    LSRK update."""
+    LSRK update. At level N the Lagrange basis is the identity on the volume points,
+    so the interpolations there (A, U, U_a, and the volume columns of b^T and a^T)
+    are copies and are not counted."""
     n1, n2, P3 = n + 1, (n + 1) ** 2, n + 3
     Np, nrow, Nfc = num_modes(n), n1 * (n1 + 1) // 2, 5 * n2
     sum_k1 = n1 * (n1 + 1) // 2  # sum_k (k+1)
     nnz_h = 3 * n1 - 2                                  # tridiagonal MH
     nnz_g = sum(min(kp + 2, n1) for kp in range(n1))    # lower Hessenberg MG
-    mac = 4 * n1 * 2 * Np                       # a pass: 2 outputs, (k+1) terms, per (f, k, j, p)
-    mac += 4 * n2 * 3 * sum_k1                  # b pass: 3 outputs per (f, k, pq), (k+1) terms
+    mac = 4 * n1 * 2 * Np - 4 * n1 ** 3         # a pass: A, dA per (f, k, j, p), (k+1) terms; A copied at level N
+    mac += 4 * n2 * 3 * sum_k1 - 8 * n1 ** 3    # b pass: U, U_a, U_b per (f, k, pq); U, U_a copied at level N
     mac += n1 * n2 * 9                          # div combination per (k, pq)
     mac += n2 * (3 * nnz_h + 2 * nnz_g)         # level mixing: al, be, div(u)_r,s with MH; ga, div(u)_c with MG
     mac += n1 * n2 * 13                         # chain rule + base lift per (k', pq)
     mac += 16 * n1 * n1 * n1                    # triangle-face c^T
-    mac += 4 * nrow * (n1 * P3 + 2 * n1)        # b^T pass
-    mac += 4 * Np * P3                          # a^T pass
+    mac += 4 * nrow * (n1 * P3 + 2 * n1) - 4 * n1 ** 3 - 8 * n1 ** 2  # b^T; level N keeps the 2 face columns
+    mac += 4 * Np * P3 - 4 * n1 ** 3            # a^T; level N keeps the 2 face columns
     return 2 * mac + Nfc * 26 + 4 * Np * 5      # flux per face point; M^{-1} (1) and LSRK (2 FMA)
 
 
 def trace_flops_per_element(n):
+    """Algorithmic flops of the trace interpolation of one element's state (Alg. 3):
+    a pass at the N+3 a points (the level-N volume columns are the coefficients
+    themselves), b pass for the base grid and the four triangle-face rows (level N is
+    the identity on the b points), c pass (level sums with G_k)."""
     n1, n2, P3 = n + 1, (n + 1) ** 2, n + 3
     Np, nB, Nfc = num_modes(n), (n + 1) ** 2 + 4 * (n + 1), 5 * n2
     sum_k1 = n1 * (n1 + 1) // 2
-    mac = 4 * P3 * Np + 4 * nB * sum_k1 + 4 * Nfc * n1
+    mac = 4 * (P3 * Np - n1 ** 3)
+    mac += 4 * (nB * sum_k1 - (n2 + 2 * n1) * n1)
+    mac += 4 * Nfc * n1
     return 2 * mac
 
 

@@ -136,6 +136,8 @@ int enqueue_steps(pyr_dg* h, int nsteps, double dt) {
     h->tr_valid = true;
     return PYR_DG_OK;
   }
+  // FP64: the trace kernel and the fused stage kernel per stage (a fused form that also
+  // interpolates the new state runs slower: its shared memory caps the resident CTAs)
   for (int n = 0; n < nsteps; ++n) {
     for (int s = 0; s < 5; ++s) {
       size_t slot = 0;

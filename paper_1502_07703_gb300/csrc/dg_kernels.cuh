@@ -172,36 +172,47 @@ struct TraceSmem {
   static constexpr size_t bytes = total * sizeof(T);
 };
 
+// The passes of the trace interpolation for one element: s_u holds its 4 Np
+// coefficients, s_A (4 nrow P3) and s_B (4 n1 (n2 + 4 n1)) are scratch, and the
+// 4 Nfc trace values go to tr_e[g*4 + f].
 template <int N, typename T>
-__global__ void __launch_bounds__(KCfg<N>::NT) trace_kernel(int64_t K, const T* __restrict__ q,
-                                                            const T* __restrict__ tab, T* __restrict__ tr) {
+__device__ __forceinline__ void trace_passes(const T* s_tab, const T* s_u, T* s_A, T* s_B, T* __restrict__ tr_e,
+                                             int tid, int nthr) {
   using d = Dims<N>;
   using S = TraceSmem<N, T>;
   constexpr TabLayout L(N);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  T* s_tab = sm + S::tab;
-  T* s_u = sm + S::u;
-  T* s_A = sm + S::A;
-  T* s_B = sm + S::B;
-  const int64_t e = blockIdx.x;
-  const int tid = threadIdx.x;
-  for (int x = tid; x < L.size; x += blockDim.x) s_tab[x] = tab[x];
-  for (int x = tid; x < 4 * d::Np; x += blockDim.x) s_u[x] = q[e * 4 * d::Np + x];
-  __syncthreads();
   // a pass: A[f][row(k,j)][p'] = sum_i l_i^k(x_p') u[f][k][j][i], p' over GL points and -1, +1.
   // Work items run level-major so that a warp's lanes share the trip count k+1.
-  for (int x = tid; x < 4 * d::nrow * d::P3; x += blockDim.x) {
-    int k = 0;
-    while (x >= 4 * d::P3 * tri_num(k + 1)) ++k;
-    const int rem = x - 4 * d::P3 * tri_num(k);
-    const int f = rem / ((k + 1) * d::P3);
-    const int j = (rem / d::P3) % (k + 1);
-    const int pp = rem % d::P3;
+  // The level-N nodes are the volume-rule points (l_i^N(x_p) = delta_ip), so level N at
+  // the volume columns is a copy; those items come last, apart from the summing ones.
+  constexpr int nLow = 4 * d::P3 * tri_num(N);       // levels below N, all columns
+  constexpr int nSum = nLow + 4 * (N + 1) * 2;       // + level N at a = -1, +1
+  for (int x = tid; x < 4 * d::nrow * d::P3; x += nthr) {
+    int k, f, j, pp;
+    if (x < nLow) {
+      k = 0;
+      while (x >= 4 * d::P3 * tri_num(k + 1)) ++k;
+      const int rem = x - 4 * d::P3 * tri_num(k);
+      f = rem / ((k + 1) * d::P3);
+      j = (rem / d::P3) % (k + 1);
+      pp = rem % d::P3;
+    } else if (x < nSum) {
+      const int rem = x - nLow;
+      k = N;
+      f = rem / (2 * (N + 1));
+      j = (rem / 2) % (N + 1);
+      pp = d::n1 + rem % 2;
+    } else {
+      const int rem = x - nSum;
+      k = N;
+      f = rem / ((N + 1) * d::n1);
+      j = (rem / d::n1) % (N + 1);
+      pp = rem % d::n1;
+    }
     const T* uc = s_u + f * d::Np + lvl_off(k) + j * (k + 1);
     const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + pp;
     T acc = 0;
-    if (k == N && pp < d::n1)  // the level-N nodes are the volume-rule points: l_i^N(x_p) = delta_ip
+    if (x >= nSum)
       acc = uc[pp];
     else
       for (int i = 0; i <= k; ++i) acc += uc[i] * lx[i * d::P3];
@@ -209,10 +220,30 @@ __global__ void __launch_bounds__(KCfg<N>::NT) trace_kernel(int64_t K, const T* 
   }
   __syncthreads();
   // b pass per level k: base grid (p,q) and the four triangle-face rows
-  for (int x = tid; x < 4 * d::n1 * S::nB; x += blockDim.x) {
-    const int s = x % S::nB;
-    const int t = x / S::nB;
-    const int f = t % 4, k = t / 4;  // level-major: equal trip counts within a warp
+  // Level-major (equal trip counts within a warp). At level N, l_j^N is the identity on
+  // the b points: only the b = -1, +1 rows sum; the base grid and the a = -1, +1 rows are
+  // copies, taken last.
+  constexpr int bLow = 4 * N * S::nB;                // levels below N
+  constexpr int bSum = bLow + 4 * 2 * d::n1;         // + level N, faces b = -1, +1
+  for (int x = tid; x < 4 * d::n1 * S::nB; x += nthr) {
+    int s, f, k;
+    if (x < bLow) {
+      s = x % S::nB;
+      const int t = x / S::nB;
+      f = t % 4;
+      k = t / 4;
+    } else if (x < bSum) {
+      const int rem = x - bLow;
+      k = N;
+      f = rem / (2 * d::n1);
+      s = d::n2 + rem % (2 * d::n1);
+    } else {
+      const int rem = x - bSum;
+      k = N;
+      f = rem / (d::n2 + 2 * d::n1);
+      s = rem % (d::n2 + 2 * d::n1);
+      if (s >= d::n2) s += 2 * d::n1;  // skip the b = -1, +1 rows
+    }
     int pa, qb;  // A column (a point) and l^k_j evaluation column (b point)
     if (s < d::n2) {
       pa = s % d::n1;
@@ -231,7 +262,7 @@ __global__ void __launch_bounds__(KCfg<N>::NT) trace_kernel(int64_t K, const T* 
     const T* Ar = s_A + (f * d::nrow + tri_num(k)) * d::P3 + pa;
     const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + qb;
     T acc = 0;
-    if (k == N && qb < d::n1)  // l_j^N(b_q) = delta_jq
+    if (x >= bSum)  // l_j^N(b_q) = delta_jq
       acc = Ar[qb * d::P3];
     else
       for (int j = 0; j <= k; ++j) acc += Ar[j * d::P3] * lx[j * d::P3];
@@ -239,7 +270,7 @@ __global__ void __launch_bounds__(KCfg<N>::NT) trace_kernel(int64_t K, const T* 
   }
   __syncthreads();
   // c pass: sum over levels with G_k(-1) (base) or G_k(c_m) (triangles)
-  for (int g = tid; g < d::Nfc; g += blockDim.x) {
+  for (int g = tid; g < d::Nfc; g += nthr) {
     const int face = g / d::n2, idx = g % d::n2;
     T out[4];
     if (face == 0) {
@@ -260,10 +291,28 @@ __global__ void __launch_bounds__(KCfg<N>::NT) trace_kernel(int64_t K, const T* 
         out[f] = acc;
       }
     }
-    T* dst = tr + (e * d::Nfc + g) * 4;
+    T* dst = tr_e + g * 4;
 #pragma unroll
     for (int f = 0; f < 4; ++f) dst[f] = out[f];
   }
+}
+
+template <int N, typename T>
+__global__ void __launch_bounds__(KCfg<N>::NT) trace_kernel(int64_t K, const T* __restrict__ q,
+                                                            const T* __restrict__ tab, T* __restrict__ tr) {
+  using d = Dims<N>;
+  using S = TraceSmem<N, T>;
+  constexpr TabLayout L(N);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* s_tab = sm + S::tab;
+  T* s_u = sm + S::u;
+  const int64_t e = blockIdx.x;
+  const int tid = threadIdx.x;
+  for (int x = tid; x < L.size; x += blockDim.x) s_tab[x] = tab[x];
+  for (int x = tid; x < 4 * d::Np; x += blockDim.x) s_u[x] = q[e * 4 * d::Np + x];
+  __syncthreads();
+  trace_passes<N, T>(s_tab, s_u, sm + S::A, sm + S::B, tr + e * d::Nfc * 4, tid, blockDim.x);
 }
 
 // ===================================================== rhs / update (a3-a7)
@@ -590,11 +639,16 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
     s_Zb[(f * d::nrow + row) * d::P3 + pp] = acc;
   }
   __syncthreads();
-  // a^T pass, M^{-1} (a6), LSRK stage (a7)
-  for (int x = tid; x < 4 * d::Np; x += nthr) {
-    const int f = x / d::Np, n = x % d::Np;
-    int k, j, i;
-    decode_mode(n, k, j, i);
+  // a^T pass, M^{-1} (a6), LSRK stage (a7). Items run level-major (k, f, j, i) so that
+  // a warp's lanes share a level: level N takes the short form below.
+  for (int y = tid; y < 4 * d::Np; y += nthr) {
+    int k = 0;
+    while (y >= 4 * lvl_off(k + 1)) ++k;
+    const int rem = y - 4 * lvl_off(k);
+    const int f = rem / ((k + 1) * (k + 1));
+    const int n = lvl_off(k) + rem % ((k + 1) * (k + 1));
+    const int j = (n - lvl_off(k)) / (k + 1), i = (n - lvl_off(k)) % (k + 1);
+    const int x = f * d::Np + n;
     const T* lx = s_tab + L.LX + (tri_num(k) + i) * d::P3;
     const T* Zr = s_Zb + (f * d::nrow + tri_num(k) + j) * d::P3;
     T acc = 0;

@@ -33,7 +33,7 @@ struct pyr_dg {
        *tab = nullptr;
   double *tabd = nullptr, *gtab = nullptr, *ev = nullptr, *partial = nullptr;
   int32_t* mapP = nullptr;
-  // FP32 handles: second trace buffer; trbuf[tr_cur] holds the traces of q when tr_valid
+  // FP32 handles: second trace buffer; {tr, tr2}[tr_cur] holds the traces of q when tr_valid
   void* tr2 = nullptr;
   int tr_cur = 0;
   bool tr_valid = false;

@@ -13,6 +13,7 @@ struct Launchers {
   cudaError_t (*prepare)();
   void (*geom)(int64_t K, const double* ev, const double* gtab, void* geo, void* gface, void* invM, cudaStream_t s);
   void (*trace)(int64_t K, const void* q, const void* tab, void* tr, cudaStream_t s);
+  // Fused stage (rhs, M^{-1}, LSRK update) reading the traces of q from tr.
   void (*rhs_update)(int64_t K, void* q, void* res, const void* tr, const int32_t* mapP, const void* geo,
                      const void* gface, const void* invM, const void* tab, int bc, double tau, double rka, double rkb,
                      double dt, const void* dt_elem, cudaStream_t s);
