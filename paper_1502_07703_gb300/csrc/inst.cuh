@@ -133,6 +133,10 @@ struct Impl {
       h[C::WFT + x] = (float)tab[L.WFT + x];
     }
     for (int k = 0; k <= N; ++k) h[C::GB + k] = (float)tab[L.GB + k];
+    for (int k = 0; k <= N; ++k)
+      for (int j = 0; j <= k; ++j)
+        for (int c = 0; c <= N; ++c)
+          h[C::CB + (tri_num(k) + j) * d::n1 + c] = (float)(tab[L.GB + k] * tab[L.LX + (tri_num(k) + j) * d::P3 + c]);
     cudaError_t e = cudaMemcpyToSymbol(c32, h, sizeof(float) * C::size);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(stage32_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S32<N>::bytes);

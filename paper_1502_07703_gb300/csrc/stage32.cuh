@@ -32,7 +32,8 @@ struct C32 {
   static constexpr int GF = GB + d::n1;             // [k][m] G_k at GJ(1,0) point m
   static constexpr int WB = GF + d::n2;             // [p + n1 q] base-face weights
   static constexpr int WFT = WB + d::n2;            // [e + n1 m] triangle-face weights
-  static constexpr int size = WFT + d::n2;
+  static constexpr int CB = WFT + d::n2;            // [tri(k)+j][c] G_k(-1) l_j^k(b_c): base trace
+  static constexpr int size = CB + d::nrow * d::n1;
 };
 
 // One copy per translation unit (each unit instantiates one degree); filled by
@@ -75,11 +76,12 @@ struct S32 {
                           bgf = bgeo + al4(d::NGEO * d::n2), binv = bgf + al4(d::NGF), bsz = binv + al4(d::Np);
   static constexpr size_t buf = al4(dl + d::nrow * d::n1);       // 2 x bsz
   static constexpr size_t Fs = buf + 2 * bsz;                    // 4 Nfc  [f][g]
-  static constexpr size_t A = Fs + 4 * d::Nfc;                   // [f][row][p]: a pass of u_old
-  static constexpr size_t dA = A + 4 * d::nrow * d::n1;          // [f][row][p]: a pass, d/da
+  static constexpr size_t A = Fs + 4 * d::Nfc;                   // [row][p][f]: a pass of u_old (float4 per (row, p))
+  static constexpr size_t dA = A + 4 * d::nrow * d::n1;          // [row][p][f]: a pass, d/da
   static constexpr size_t ZA = 4 * d::nrow * YS > 8 * d::nrow * d::n1 ? 4 * d::nrow * YS : 8 * d::nrow * d::n1;
   static constexpr size_t Y = A + ZA;                            // 4 n1 nY  [f][k][p'][q']
-  static constexpr size_t total = Y + 4 * d::n1 * nY;
+  static constexpr size_t dec = Y + 4 * d::n1 * nY;             // Np mode decodings k | j << 8 | i << 16
+  static constexpr size_t total = dec + d::Np;
   static constexpr size_t Z = A;                                 // 4 nrow YS [f][row][p'] (A, dA dead by then)
   static_assert(4 * d::nrow * d::P3 <= ZA, "trace a pass (At) aliases the A/dA region");
   // resident CTAs per SM the register budget is tuned for
@@ -111,7 +113,13 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
   float* s_dA = sm + S::dA;
   float* s_Y = sm + S::Y;
   float* s_Z = sm + S::Z;
+  int* s_dec = reinterpret_cast<int*>(sm + S::dec);
   const int tid = threadIdx.x;
+  for (int n = tid; n < Np; n += S::NT) {
+    int k, j, i;
+    decode_mode(n, k, j, i);
+    s_dec[n] = k | j << 8 | i << 16;
+  }
 
   for (int x = tid; x < nrow * P3; x += S::NT) s_lx[x] = c32[C::LX + x];
   for (int x = tid; x < nrow * n1; x += S::NT) s_dl[x] = c32[C::DL + x];
@@ -192,7 +200,7 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
           }
           // the level-N nodes are the volume-rule points: l_i^N(a_p) = delta_ip
           if (k == N) a = uf[lvl_off(k) + j * (k + 1) + p];
-          const int o = (f * nrow + tri_num(k) + j) * n1 + p;
+          const int o = ((tri_num(k) + j) * n1 + p) * 4 + f;
           s_A[o] = a;
           s_dA[o] = da;
         }
@@ -229,27 +237,37 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
               if (k < N) lq[j] = s_lx[(tri_num(k) + j) * P3 + qq];
               dlq[j] = s_dl[(tri_num(k) + j) * n1 + qq];
             }
+            // the three velocity fields of A, dA at (row, p) in one float4 each
+            float v[3] = {0.f, 0.f, 0.f}, va[3] = {0.f, 0.f, 0.f}, vb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int j = 0; j <= k; ++j) {
+              const int o = ((tri_num(k) + j) * n1 + p) * 4;
+              const float4 a4 = *reinterpret_cast<const float4*>(s_A + o);
+              const float a3[3] = {a4.y, a4.z, a4.w};
+#pragma unroll
+              for (int m = 0; m < 3; ++m) vb[m] = fmaf(a3[m], dlq[j], vb[m]);
+              if (k < N) {
+                const float4 d4 = *reinterpret_cast<const float4*>(s_dA + o);
+                const float d3[3] = {d4.y, d4.z, d4.w};
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                  v[m] = fmaf(a3[m], lq[j], v[m]);
+                  va[m] = fmaf(d3[m], lq[j], va[m]);
+                }
+              }
+            }
+            if (k == N) {  // l_j^N(b_q) = delta_jq
+              const int o = ((tri_num(k) + qq) * n1 + p) * 4;
+              const float4 a4 = *reinterpret_cast<const float4*>(s_A + o);
+              const float4 d4 = *reinterpret_cast<const float4*>(s_dA + o);
+              v[0] = a4.y, v[1] = a4.z, v[2] = a4.w;
+              va[0] = d4.y, va[1] = d4.z, va[2] = d4.w;
+            }
             float xs = 0.f, zs = 0.f;
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
-              float v = 0.f, va = 0.f, vb = 0.f;
-#pragma unroll
-              for (int j = 0; j <= k; ++j) {
-                const int o = ((m + 1) * nrow + tri_num(k) + j) * n1 + p;
-                const float a = s_A[o];
-                vb = fmaf(a, dlq[j], vb);
-                if (k < N) {
-                  v = fmaf(a, lq[j], v);
-                  va = fmaf(s_dA[o], lq[j], va);
-                }
-              }
-              if (k == N) {  // l_j^N(b_q) = delta_jq
-                const int o = ((m + 1) * nrow + tri_num(k) + qq) * n1 + p;
-                v = s_A[o];
-                va = s_dA[o];
-              }
-              xs = fmaf(g[m], va, fmaf(g[3 + m], vb, xs));
-              zs = fmaf(g[6 + m], v, zs);
+              xs = fmaf(g[m], va[m], fmaf(g[3 + m], vb[m], xs));
+              zs = fmaf(g[6 + m], v[m], zs);
             }
             X[k] = xs;
             Zc[k] = zs;
@@ -273,7 +291,7 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
             float u = 0.f, ua = 0.f, ub = 0.f;
 #pragma unroll
             for (int j = 0; j <= k; ++j) {
-              const int o = (tri_num(k) + j) * n1 + p;
+              const int o = ((tri_num(k) + j) * n1 + p) * 4;
               const float a = s_A[o];
               ub = fmaf(a, s_dl[(tri_num(k) + j) * n1 + qq], ub);
               if (k < N) {
@@ -283,7 +301,7 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
               }
             }
             if (k == N) {  // l_j^N(b_q) = delta_jq
-              const int o = (tri_num(k) + qq) * n1 + p;
+              const int o = ((tri_num(k) + qq) * n1 + p) * 4;
               u = s_A[o];
               ua = s_dA[o];
             }
@@ -369,10 +387,11 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
     __syncthreads();
 
     // ---- a^T pass, M^{-1} (a6), LSRK update (a7); the new state goes back to shared memory
+    const float dte = dt_elem ? dt_elem[e] : dt;  // per-element step when meshes are batched
     for (int x = tid; x < 4 * Np; x += S::NT) {
       const int f = x / Np, n = x - f * Np;
-      int k, j, i;
-      decode_mode(n, k, j, i);
+      const int kji = s_dec[n];
+      const int k = kji & 0xff, j = (kji >> 8) & 0xff, i = kji >> 16;
       const float* Zr = s_Z + (f * nrow + tri_num(k) + j) * YS;
       const float* lr = s_lx + (tri_num(k) + i) * P3;
       float acc = 0.f;
@@ -384,7 +403,6 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
       }
       const float rhs = -s_inv[n] * acc;
       const int64_t gi = e * 4 * Np + x;
-      const float dte = dt_elem ? dt_elem[e] : dt;  // per-element step when meshes are batched
       const float rnew = fmaf(rka, s_res[x], dte * rhs);
       res[gi] = rnew;
       const float unew = fmaf(rkb, rnew, s_u[x]);
@@ -420,10 +438,10 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
     }
     __syncthreads();
     // then the face points: 16 n1 items for the four triangular faces (a level sum,
-    // then the c direction), 4 n2 items for the base
+    // then the c direction), 4 n1 items for the base (one a point, all b points)
     {
       float* dst = tr_nxt + e * Nfc * 4;
-      for (int x = tid; x < 16 * n1 + 4 * n2; x += S::NT) {
+      for (int x = tid; x < 20 * n1; x += S::NT) {
         if (x < 16 * n1) {
           const int f = x & 3, y = x >> 2;
           const int t = y % n1, kind = y / n1;  // kind: 0 b=-1, 1 b=+1, 2 a=-1, 3 a=+1
@@ -455,28 +473,22 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
             for (int k = 0; k <= N; ++k) acc = fmaf(c32[C::GF + k * n1 + m], Sk[k], acc);
             dst[4 * (face * n2 + t + n1 * m) + f] = acc;
           }
-        } else {  // base (c = -1) at (a_t, b_c)
+        } else {  // base (c = -1) at (a_t, b_c) for every c
           const int y = x - 16 * n1;
-          const int f = y & 3, z = y >> 2;
-          const int t = z % n1, c = z / n1;
+          const int f = y & 3, t = y >> 2;
           const float* Ar = s_At + f * nrow * P3 + t;
-          const float* wr = s_lx + c;
-          float acc = 0.f;
+          float at[nrow];
 #pragma unroll
-          for (int k = 0; k <= N; ++k) {
-            float sacc = 0.f;
-            if (k == N) {  // l_j^N(b_c) = delta_jc and At[N][pp < n1] is u
-              sacc = s_u[f * Np + lvl_off(N) + c * n1 + t];
-            } else {
+          for (int r = 0; r < tri_num(N); ++r) at[r] = Ar[r * P3];
 #pragma unroll
-              for (int j = 0; j <= k; ++j) {
-                const int r = tri_num(k) + j;
-                sacc = fmaf(wr[r * P3], Ar[r * P3], sacc);
-              }
-            }
-            acc = fmaf(c32[C::GB + k], sacc, acc);
+          for (int c = 0; c <= N; ++c) {
+            float acc = 0.f;
+#pragma unroll
+            for (int r = 0; r < tri_num(N); ++r) acc = fmaf(c32[C::CB + r * n1 + c], at[r], acc);
+            // level N: l_j^N(b_c) = delta_jc and At[N][t < n1] is u
+            acc = fmaf(c32[C::GB + N], s_u[f * Np + lvl_off(N) + c * n1 + t], acc);
+            dst[4 * (t + n1 * c) + f] = acc;
           }
-          dst[4 * (t + n1 * c) + f] = acc;
         }
       }
     }
