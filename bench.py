@@ -43,6 +43,19 @@ METRIC = "pyramid DOF-updates/s per RK stage"
 SAMPLE_NX = 8  # oracle sample: 8^3 hexes x 6 = 3072 pyramids, same N, perturbation and seed
 
 
+def _hbm_peak():
+    """Measured copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json beside this file),
+    else the earlier single measurement of 6.8 TB/s, with which one it is."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+HBM_GBS, HBM_KIND = _hbm_peak()
+
+
 def num_modes(n):
     return (n + 1) * (n + 2) * (2 * n + 3) // 6
 
@@ -72,6 +85,16 @@ def rhs_flops_per_element(n):
     mac += 4 * nrow * (n1 * P3 + 2 * n1) - 4 * n1 ** 3 - 8 * n1 ** 2  # b^T; level N keeps the 2 face columns
     mac += 4 * Np * P3 - 4 * n1 ** 3            # a^T; level N keeps the 2 face columns
     return 2 * mac + Nfc * 26 + 4 * Np * 5      # flux per face point; M^{-1} (1) and LSRK (2 FMA)
+
+
+def stage_bytes_per_element(n, tb):
+    """Algorithmic DRAM bytes of one fused stage per element with tb-byte values: state
+    and residual read and written, own and neighbour traces read and the new traces
+    written (the FP32 kernel; the FP64 path writes them from the trace kernel), the 9
+    geometric factors per (a,b) point, face geometry, M^{-1} and the connectivity."""
+    n1, n2 = n + 1, (n + 1) ** 2
+    Np, Nfc = num_modes(n), 5 * n2
+    return tb * (4 * 4 * Np + 3 * 4 * Nfc + 9 * n2 + 16 + 4 * n2 + Np) + 4 * Nfc
 
 
 def trace_flops_per_element(n):
@@ -248,6 +271,16 @@ def measure_form(binding, nx, delta, seed, n, precision, steps, warmup, dev):
            "trace_kernel_ms": prof["trace"][0] / prof["trace"][1] if prof["trace"][1] else 0.0,
            "launches_per_step": (prof["rhs"][1] + prof["trace"][1]) / steps,
            "l2_rel_error_vs_exact": err_rel, "t_end": (warmup + steps) * dt}
+    if precision == "f32":  # the stage kernel against the FP32 FMA and HBM peaks
+        t_s = out["stage_kernel_ms"] * 1e-3
+        flops = (rhs_flops_per_element(n) + trace_flops_per_element(n)) * s.K / t_s / 1e12
+        gbs = stage_bytes_per_element(n, 4) * s.K / t_s / 1e9
+        peak = binding.fma_peak("f32")
+        out["stage_kernel_roofline"] = {"achieved_tflops": flops, "fp32_fma_peak_tflops": peak,
+                                        "alu_frac": flops / peak, "algorithmic_bytes_per_element":
+                                        stage_bytes_per_element(n, 4), "achieved_gbs": gbs,
+                                        "hbm_peak_gbs": HBM_GBS, "hbm_peak_kind": HBM_KIND,
+                                        "hbm_frac": gbs / HBM_GBS}
     s.close()
     return out
 
@@ -442,12 +475,14 @@ def main():
     tr_ms, tr_n = prof["trace"]
     peak = binding.fma_peak(prec)
     rhs_avg_s = rhs_ms / rhs_n * 1e-3
-    achieved = rhs_flops_per_element(nd) * K / rhs_avg_s / 1e12
+    # the FP32 stage kernel also interpolates the new state to the face points
+    flops_el = rhs_flops_per_element(nd) + (trace_flops_per_element(nd) if prec == "f32" else 0)
+    achieved = flops_el * K / rhs_avg_s / 1e12
     # DRAM bytes per launch of the fused stage kernel from an ncu capture of this kernel
     # version (scaled by the element count); None until one is taken.
     traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": f"rhs_kernel<{nd},{'double' if prec == 'f64' else 'float'},update>",
+                "traffic": traffic, "kernel": f"rhs_kernel<{nd},double,update>" if prec == "f64" else f"stage32_kernel<{nd}>",
                 "peak_kind": f"{prec.upper()} FMA throughput measured in this run",
                 "kernel_ms_avg": rhs_ms / rhs_n, "trace_kernel_ms_avg": tr_ms / tr_n if tr_n else 0.0,
                 "kernel_share": rhs_ms / (rhs_ms + tr_ms)}
