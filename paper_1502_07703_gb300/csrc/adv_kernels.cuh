@@ -54,15 +54,30 @@ __global__ void __launch_bounds__(KCfg<N>::NT) trace1_kernel(int64_t K, const T*
   for (int x = tid; x < L.size; x += nthr) s_tab[x] = tab[x];
   for (int x = tid; x < d::Np; x += nthr) s_u[x] = q[e * d::Np + x];
   __syncthreads();
+  // a pass; at level N the volume columns are copies (l_i^N(x_p) = delta_ip), taken last
+  constexpr int nLow = tri_num(N) * d::P3, nSum = nLow + (N + 1) * 2;
   for (int x = tid; x < d::nrow * d::P3; x += nthr) {
-    const int pp = x % d::P3, row = x / d::P3;
+    int pp, row;
+    if (x < nLow) {
+      pp = x % d::P3;
+      row = x / d::P3;
+    } else if (x < nSum) {
+      pp = d::n1 + (x - nLow) % 2;
+      row = tri_num(N) + (x - nLow) / 2;
+    } else {
+      pp = (x - nSum) % d::n1;
+      row = tri_num(N) + (x - nSum) / d::n1;
+    }
     int k, j;
     decode_row(row, k, j);
     const T* uc = s_u + lvl_off(k) + j * (k + 1);
     const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + pp;
     T acc = 0;
-    for (int i = 0; i <= k; ++i) acc += uc[i] * lx[i * d::P3];
-    s_A[x] = acc;
+    if (x >= nSum)
+      acc = uc[pp];
+    else
+      for (int i = 0; i <= k; ++i) acc += uc[i] * lx[i * d::P3];
+    s_A[row * d::P3 + pp] = acc;
   }
   __syncthreads();
   for (int x = tid; x < d::n1 * S::nB; x += nthr) {
@@ -84,7 +99,10 @@ __global__ void __launch_bounds__(KCfg<N>::NT) trace1_kernel(int64_t K, const T*
     const T* Ar = s_A + tri_num(k) * d::P3 + pa;
     const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + qb;
     T acc = 0;
-    for (int j = 0; j <= k; ++j) acc += Ar[j * d::P3] * lx[j * d::P3];
+    if (k == N && qb < d::n1)  // l_j^N(b_q) = delta_jq
+      acc = Ar[qb * d::P3];
+    else
+      for (int j = 0; j <= k; ++j) acc += Ar[j * d::P3] * lx[j * d::P3];
     s_B[k * S::nB + s] = acc;
   }
   __syncthreads();
@@ -174,9 +192,14 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
     const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + p;
     const T* dl = s_tab + L.DL + tri_num(k) * d::n1 + p;
     T a = 0, da = 0;
-    for (int i = 0; i <= k; ++i) {
-      a += uc[i] * lx[i * d::P3];
-      da += uc[i] * dl[i * d::n1];
+    if (k == N) {  // l_i^N(a_p) = delta_ip
+      a = uc[p];
+      for (int i = 0; i <= k; ++i) da += uc[i] * dl[i * d::n1];
+    } else {
+      for (int i = 0; i <= k; ++i) {
+        a += uc[i] * lx[i * d::P3];
+        da += uc[i] * dl[i * d::n1];
+      }
     }
     s_A[x] = a;
     s_dA[x] = da;
@@ -190,11 +213,17 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
     const T* lx = s_tab + L.LX + tri_num(k) * d::P3 + q;
     const T* dl = s_tab + L.DL + tri_num(k) * d::n1 + q;
     T u = 0, ua = 0, ub = 0;
-    for (int j = 0; j <= k; ++j) {
-      const T av = Ar[j * d::n1], lv = lx[j * d::P3];
-      u += av * lv;
-      ub += av * dl[j * d::n1];
-      ua += dAr[j * d::n1] * lv;
+    if (k == N) {  // l_j^N(b_q) = delta_jq
+      u = Ar[q * d::n1];
+      ua = dAr[q * d::n1];
+      for (int j = 0; j <= k; ++j) ub += Ar[j * d::n1] * dl[j * d::n1];
+    } else {
+      for (int j = 0; j <= k; ++j) {
+        const T av = Ar[j * d::n1], lv = lx[j * d::P3];
+        u += av * lv;
+        ub += av * dl[j * d::n1];
+        ua += dAr[j * d::n1] * lv;
+      }
     }
     s_U[x] = u;
     s_Ua[x] = ua;
@@ -243,7 +272,12 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
     const T* Yr = s_Y + (k * d::P3 + pp) * d::P3;
     const T* lx = s_tab + L.LX + (tri_num(k) + j) * d::P3;
     T acc = 0;
-    for (int c = 0; c < d::P3; ++c) acc += lx[c] * Yr[c];
+    if (k == N) {  // l_j^N(x_c) = delta_jc on the volume points; the face columns remain
+      acc = Yr[j];
+      for (int c = d::n1; c < d::P3; ++c) acc += lx[c] * Yr[c];
+    } else {
+      for (int c = 0; c < d::P3; ++c) acc += lx[c] * Yr[c];
+    }
     s_Zb[row * d::P3 + pp] = acc;
   }
   __syncthreads();
@@ -253,7 +287,11 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
     const T* lx = s_tab + L.LX + (tri_num(k) + i) * d::P3;
     const T* Zr = s_Zb + (tri_num(k) + j) * d::P3;
     T acc = 0;
-    for (int c = 0; c < d::P3; ++c) acc += lx[c] * Zr[c];
+    if (k == N) {  // l_i^N(x_c) = delta_ic on the volume points; the face columns remain
+      acc = Zr[i] + lx[d::n1] * Zr[d::n1] + lx[d::n1 + 1] * Zr[d::n1 + 1];
+    } else {
+      for (int c = 0; c < d::P3; ++c) acc += lx[c] * Zr[c];
+    }
     const T rhs = -invM[e * d::Np + n] * acc;
     const int64_t gi = e * d::Np + n;
     if (UPDATE) {
