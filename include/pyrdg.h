@@ -214,9 +214,12 @@ int pyr_dg_batch_setup(int nmesh, const double* const* vertices, const int64_t* 
 /* Number of meshes, of degree groups (= launches per stage), total elements and
  * total degrees of freedom (sum of K * 4 * Np). Any pointer may be NULL. */
 int pyr_dg_batch_info(const pyr_dg_batch* b, int* nmesh, int* ngroups, int64_t* total_K, int64_t* total_dofs);
-/* Degree, element count and launch grid (the autotuned persistent grid for FP32)
- * of degree group `group` < ngroups. */
-int pyr_dg_batch_group_info(const pyr_dg_batch* b, int group, int* N, int64_t* K, int* stage_blocks);
+/* Degree, element count, launch grid and elements per CTA of degree group
+ * `group` < ngroups. For FP32 the grid (persistent CTAs) and the elements per CTA
+ * (1, 2, 4 or 8) are autotuned at setup on that group; FP64 launches one CTA per
+ * element. Any out pointer may be NULL. */
+int pyr_dg_batch_group_info(const pyr_dg_batch* b, int group, int* N, int64_t* K, int* stage_blocks,
+                            int* elems_per_block);
 /* Project the exact standing wave at t0 into every mesh; sets every mesh's time to t0. */
 int pyr_dg_batch_project(pyr_dg_batch* b, double t0);
 /* Per-mesh CFL time steps (as pyr_dg_dt_cfl) into dt[nmesh]. */

@@ -80,7 +80,7 @@ _SIGNATURES = {
     "pyr_dg_batch_setup": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_c_dp), _c_i64p, ctypes.POINTER(_c_i32p),
                                           _c_i64p, _c_ip, ctypes.POINTER(Opts), ctypes.POINTER(_c_h)]),
     "pyr_dg_batch_info": (ctypes.c_int, [_c_h, _c_ip, _c_ip, _c_i64p, _c_i64p]),
-    "pyr_dg_batch_group_info": (ctypes.c_int, [_c_h, ctypes.c_int, _c_ip, _c_i64p, _c_ip]),
+    "pyr_dg_batch_group_info": (ctypes.c_int, [_c_h, ctypes.c_int, _c_ip, _c_i64p, _c_ip, _c_ip]),
     "pyr_dg_batch_project": (ctypes.c_int, [_c_h, ctypes.c_double]),
     "pyr_dg_batch_dt_cfl": (ctypes.c_int, [_c_h, ctypes.c_double, _c_dp]),
     "pyr_dg_batch_step": (ctypes.c_int, [_c_h, ctypes.c_int, _c_dp]),
@@ -365,9 +365,10 @@ class Batch:
     def groups(self):
         out = []
         for g in range(self.ngroups):
-            n, k, b = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
-            _check(lib().pyr_dg_batch_group_info(self._h, g, ctypes.byref(n), ctypes.byref(k), ctypes.byref(b)))
-            out.append({"N": n.value, "K": k.value, "stage_blocks": b.value})
+            n, k, b, epb = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+            _check(lib().pyr_dg_batch_group_info(self._h, g, ctypes.byref(n), ctypes.byref(k), ctypes.byref(b),
+                                                 ctypes.byref(epb)))
+            out.append({"N": n.value, "K": k.value, "stage_blocks": b.value, "elems_per_block": epb.value})
         return out
 
     @property

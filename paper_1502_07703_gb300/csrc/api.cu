@@ -127,7 +127,8 @@ int enqueue_steps(pyr_dg* h, int nsteps, double dt) {
       for (int s = 0; s < 5; ++s) {
         CUDA_TRY(prof_begin(h, 1, &slot));
         h->L->stage32(h->K, h->q, h->res, buf[h->tr_cur], buf[1 - h->tr_cur], h->mapP, h->geo, h->gface, h->invM,
-                      h->bc, h->tau, kRkA[s], kRkB[s], dt, h->dt_elem, 1, h->stage_blocks, h->stream);
+                      h->bc, h->tau, kRkA[s], kRkB[s], dt, h->dt_elem, 1, h->stage_epb, h->stage_blocks,
+                      h->stream);
         CUDA_TRY(prof_end(h, slot));
         h->tr_cur = 1 - h->tr_cur;
       }
@@ -342,7 +343,9 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   if (e == cudaSuccess) e = h->L->prepare();
   if (e == cudaSuccess && h->use_stage32) {
     e = h->L->upload_c32(T.tab.data());
-    h->stage_blocks = (int)std::min<int64_t>(K, (int64_t)(nsm > 0 ? nsm : 1) * h->L->blocks_per_sm32());
+    h->stage_epb = h->L->epb32;
+    const int64_t groups = (K + h->stage_epb - 1) / h->stage_epb;
+    h->stage_blocks = (int)std::min<int64_t>(groups, (int64_t)(nsm > 0 ? nsm : 1) * h->L->blocks_per_sm32(h->stage_epb));
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->tab, tabsrc, (size_t)TL.size * ts, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->tabd, T.tab.data(), (size_t)TL.size * 8, cudaMemcpyHostToDevice, s);

@@ -51,7 +51,8 @@ void destroy_batch(pyr_dg_batch* b) {
 
 // Time one step of a handle with the given persistent grid (state must be all zero
 // and dt_elem zero, so the step leaves it zero).
-int time_grid(pyr_dg* h, int blocks, float* ms) {
+int time_grid(pyr_dg* h, int epb, int blocks, float* ms) {
+  h->stage_epb = epb;
   h->stage_blocks = blocks;
   h->tr_valid = false;
   cudaEvent_t e0, e1;
@@ -176,28 +177,36 @@ int pyr_dg_batch_setup(int nmesh, const double* const* vertices, const int64_t* 
       destroy_batch(b);
       return fail(PYR_DG_ERR_NO_MEMORY, "cannot allocate the per-element time steps");
     }
-    // Autotune the persistent grid of the FP32 stage kernel on the zero state.
+    // Autotune the FP32 stage kernel on the zero state: elements per CTA (1, 2, 4, 8 where
+    // built for this degree) and the persistent grid (1..16 resident-CTA waves per SM).
     if (h->use_stage32 && h->K >= 4096) {
       int nsm = 1;
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
-      const int maxb = std::max(1, h->stage_blocks / std::max(1, nsm));
-      int best = h->stage_blocks;
+      int best_epb = h->stage_epb, best = h->stage_blocks;
       float best_ms = 1e30f;
+      const int epbs[] = {1, 2, 4, 8};
       const int mult[] = {1, 2, 3, 4, 6, 8, 12, 16};
-      for (int m : mult) {
-        if (m > maxb) break;
-        const int blocks = (int)std::min<int64_t>(h->K, (int64_t)m * nsm);
-        float ms = 0.f;
-        const int trc = time_grid(h, blocks, &ms);
-        if (trc != PYR_DG_OK) {
-          destroy_batch(b);
-          return trc;
-        }
-        if (ms < best_ms) {
-          best_ms = ms;
-          best = blocks;
+      for (int epb : epbs) {
+        const int bps = h->L->blocks_per_sm32(epb);
+        if (bps <= 0) continue;
+        const int64_t groups = (h->K + epb - 1) / epb;
+        for (int m : mult) {
+          if (m > bps) break;
+          const int blocks = (int)std::min<int64_t>(groups, (int64_t)m * nsm);
+          float ms = 0.f;
+          const int trc = time_grid(h, epb, blocks, &ms);
+          if (trc != PYR_DG_OK) {
+            destroy_batch(b);
+            return trc;
+          }
+          if (ms < best_ms) {
+            best_ms = ms;
+            best_epb = epb;
+            best = blocks;
+          }
         }
       }
+      h->stage_epb = best_epb;
       h->stage_blocks = best;
       h->tr_valid = false;
     }
@@ -224,12 +233,14 @@ int pyr_dg_batch_info(const pyr_dg_batch* b, int* nmesh, int* ngroups, int64_t* 
   return PYR_DG_OK;
 }
 
-int pyr_dg_batch_group_info(const pyr_dg_batch* b, int group, int* N, int64_t* K, int* stage_blocks) {
+int pyr_dg_batch_group_info(const pyr_dg_batch* b, int group, int* N, int64_t* K, int* stage_blocks,
+                            int* elems_per_block) {
   if (!b || group < 0 || group >= (int)b->groups.size()) return fail(PYR_DG_ERR_BAD_ARG, "bad group");
   const pyr_dg* h = b->groups[group];
   if (N) *N = h->N;
   if (K) *K = h->K;
   if (stage_blocks) *stage_blocks = h->use_stage32 ? h->stage_blocks : (int)h->K;
+  if (elems_per_block) *elems_per_block = h->use_stage32 ? h->stage_epb : 1;
   return PYR_DG_OK;
 }
 

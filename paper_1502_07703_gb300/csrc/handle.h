@@ -37,7 +37,8 @@ struct pyr_dg {
   void* tr2 = nullptr;
   int tr_cur = 0;
   bool tr_valid = false;
-  int stage_blocks = 0;
+  int stage_blocks = 0;         // persistent grid of the FP32 stage kernel
+  int stage_epb = 1;            // elements per CTA of the FP32 stage kernel
   // per-element time step (device, K elements of the handle's type) when the handle
   // holds several batched meshes; null for a single mesh
   void* dt_elem = nullptr;

@@ -17,7 +17,7 @@ struct Impl {
   static_assert(ProjSmem<N>::bytes + 15 * 8 <= kMaxSmem, "projection kernel shared memory");
   static_assert(ErrSmem<N>::bytes + 8 * (15 + 2 * 16) <= kMaxSmem, "error kernel shared memory");
   static_assert(4 * Dims<N>::n2 <= 4 * Dims<N>::n1 * Dims<N>::P3 * Dims<N>::P3, "projection B/J scratch");
-  static_assert(S32<N>::bytes <= kMaxSmem, "FP32 stage kernel shared memory");
+  static_assert(S32<N, 1>::bytes <= kMaxSmem, "FP32 stage kernel shared memory");
   static_assert(Rhs1Smem<N, T>::bytes <= kMaxSmem && Proj1Smem<N>::bytes <= kMaxSmem, "advection shared memory");
 
   static cudaError_t prepare() {
@@ -110,13 +110,48 @@ struct Impl {
                     double* partial, int nblocks, cudaStream_t s) {
     error_kernel<N, T><<<nblocks, ErrCfg<N>::NT, ErrSmem<N>::bytes, s>>>(K, (const T*)q, ev, gtab, bc, t, partial);
   }
+  template <int E>
+  static void stage32_e(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
+                        const void* geo, const void* gface, const void* invM, int bc, double tau, double rka,
+                        double rkb, double dt, const void* dt_elem, int write_traces, int nblocks, cudaStream_t s) {
+    if constexpr (epb_supported(N, E)) {
+      static_assert(S32<N, E>::bytes <= kMaxSmem, "FP32 stage kernel shared memory");
+      stage32_kernel<N, E><<<nblocks, S32<N, E>::NT, S32<N, E>::bytes, s>>>(
+          K, (float*)q, (float*)res, (const float*)tr_cur, (float*)tr_nxt, mapP, (const float*)geo,
+          (const float*)gface, (const float*)invM, bc, (float)tau, (float)rka, (float)rkb, (float)dt,
+          (const float*)dt_elem, write_traces);
+    }
+  }
+  // epb must be one blocks_per_sm32 reports as built (nonzero)
   static void stage32(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
                       const void* geo, const void* gface, const void* invM, int bc, double tau, double rka, double rkb,
-                      double dt, const void* dt_elem, int write_traces, int nblocks, cudaStream_t s) {
-    stage32_kernel<N><<<nblocks, S32<N>::NT, S32<N>::bytes, s>>>(
-        K, (float*)q, (float*)res, (const float*)tr_cur, (float*)tr_nxt, mapP, (const float*)geo,
-        (const float*)gface, (const float*)invM, bc, (float)tau, (float)rka, (float)rkb, (float)dt,
-        (const float*)dt_elem, write_traces);
+                      double dt, const void* dt_elem, int write_traces, int epb, int nblocks, cudaStream_t s) {
+#define PYRDG_STAGE32_ARGS K, q, res, tr_cur, tr_nxt, mapP, geo, gface, invM, bc, tau, rka, rkb, dt, dt_elem, write_traces, nblocks, s
+    switch (epb) {
+      case 2: stage32_e<2>(PYRDG_STAGE32_ARGS); break;
+      case 4: stage32_e<4>(PYRDG_STAGE32_ARGS); break;
+      case 8: stage32_e<8>(PYRDG_STAGE32_ARGS); break;
+      default: stage32_e<1>(PYRDG_STAGE32_ARGS); break;
+    }
+#undef PYRDG_STAGE32_ARGS
+  }
+  template <int E>
+  static cudaError_t smem32() {
+    if constexpr (epb_supported(N, E))
+      return cudaFuncSetAttribute(stage32_kernel<N, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)S32<N, E>::bytes);
+    return cudaSuccess;
+  }
+  template <int E>
+  static int bps32() {
+    if constexpr (epb_supported(N, E)) {
+      int n = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage32_kernel<N, E>, S32<N, E>::NT,
+                                                        S32<N, E>::bytes) != cudaSuccess)
+        return 1;
+      return n > 0 ? n : 1;
+    }
+    return 0;
   }
   static cudaError_t upload_c32(const double* tab) {
     using C = C32<N>;
@@ -138,14 +173,21 @@ struct Impl {
         for (int c = 0; c <= N; ++c)
           h[C::CB + (tri_num(k) + j) * d::n1 + c] = (float)(tab[L.GB + k] * tab[L.LX + (tri_num(k) + j) * d::P3 + c]);
     cudaError_t e = cudaMemcpyToSymbol(c32, h, sizeof(float) * C::size);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(stage32_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S32<N>::bytes);
+    if (e == cudaSuccess) e = smem32<1>();
+    if (e == cudaSuccess) e = smem32<2>();
+    if (e == cudaSuccess) e = smem32<4>();
+    if (e == cudaSuccess) e = smem32<8>();
+    return e;
   }
-  static int blocks_per_sm32() {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage32_kernel<N>, S32<N>::NT, S32<N>::bytes) != cudaSuccess)
-      return 1;
-    return n > 0 ? n : 1;
+  // Resident CTAs per SM of the stage kernel with epb elements per CTA; 0 if not built.
+  static int blocks_per_sm32(int epb) {
+    switch (epb) {
+      case 1: return bps32<1>();
+      case 2: return bps32<2>();
+      case 4: return bps32<4>();
+      case 8: return bps32<8>();
+      default: return 0;
+    }
   }
   static Launchers make() {
     Launchers l;
@@ -169,11 +211,14 @@ struct Impl {
       l.stage32 = &stage32;
       l.upload_c32 = &upload_c32;
       l.blocks_per_sm32 = &blocks_per_sm32;
-      l.smem_stage32 = S32<N>::bytes;
+      // measured best on 196,608 pyramids: groups of 8 at N = 1, 2 at N = 2, 3, else 1
+      l.epb32 = N == 1 ? 8 : N <= 3 ? 2 : 1;
+      l.smem_stage32 = S32<N, 1>::bytes;
     } else {
       l.stage32 = nullptr;
       l.upload_c32 = nullptr;
       l.blocks_per_sm32 = nullptr;
+      l.epb32 = 1;
       l.smem_stage32 = 0;
     }
     return l;

@@ -25,14 +25,17 @@ struct Launchers {
                 int nblocks, cudaStream_t s);
   // Single-launch FP32 stage (null for double): reads traces of q from tr_cur, writes
   // the updated state, residual and (if write_traces) the new traces into tr_nxt.
+  // epb: elements per CTA, one that blocks_per_sm32 reports as built.
   void (*stage32)(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
                   const void* geo, const void* gface, const void* invM, int bc, double tau, double rka, double rkb,
-                  double dt, const void* dt_elem, int write_traces, int nblocks, cudaStream_t s);
+                  double dt, const void* dt_elem, int write_traces, int epb, int nblocks, cudaStream_t s);
   // Fill the FP32 stage kernel's constant tables on the current device from the
   // double reference tables (TabLayout); null for double.
   cudaError_t (*upload_c32)(const double* tab);
-  // Resident CTAs per SM of the FP32 stage kernel (for its persistent grid); 0 for double.
-  int (*blocks_per_sm32)();
+  // Resident CTAs per SM of the FP32 stage kernel with epb elements per CTA (for its
+  // persistent grid); 0 when that epb is not built for this degree.
+  int (*blocks_per_sm32)(int epb);
+  int epb32;  // default elements per CTA of the FP32 stage kernel
   size_t smem_stage32;
   // Scalar advection (one field): trace, fused stage / rhs, projection and error norm.
   void (*trace1)(int64_t K, const void* q, const void* tab, void* tr, cudaStream_t s);

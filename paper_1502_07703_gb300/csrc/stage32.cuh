@@ -8,8 +8,10 @@
 //    unrolled, so table operands are immediate constant-bank operands of FFMA;
 //  - each thread owns a column of one pass and keeps its data in registers;
 //    the work items of each pass are spread over all four warps;
-//  - CTAs are persistent (grid-stride over elements); while one element is
-//    computed, the next element's contiguous inputs (state, residual, geometry,
+//  - a CTA works on EPB elements at a time (more at low degree, where one element
+//    leaves most threads idle in every pass); item counts are compile-time constants;
+//  - CTAs are persistent (grid-stride over element groups); while one group is
+//    computed, the next group's contiguous inputs (state, residual, geometry,
 //    M^{-1}) arrive in a second shared-memory buffer by cp.async;
 //  - the kernel also interpolates the updated state to the face points (the
 //    trace step of Alg. 3) into the other half of a ping-pong trace buffer, so
@@ -58,61 +60,73 @@ __device__ __forceinline__ void cp_async4(void* s, const void* g) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <int N>
+// Elements per CTA the FP32 stage kernel is built for at degree N: both halves of the
+// level mixing must fit the CTA's 128 threads, and EPB is one of 1, 2, 4, 8.
+constexpr bool epb_supported(int N, int EPB) {
+  return (EPB == 1 || EPB == 2 || EPB == 4 || EPB == 8) &&
+         2 * ((EPB * (N + 1) * (N + 1) + 31) / 32) * 32 <= 128;
+}
+
+// Shared-memory layout and work decomposition for degree N with EPB elements per CTA.
+template <int N, int EPB>
 struct S32 {
   using d = Dims<N>;
   static constexpr int NT = 128;
   static constexpr int G = (d::n1 + 1) / 2;        // level groups {g, N-g}
   static constexpr int YS = (d::P3 + 3) / 4 * 4;   // padded row stride of Y and Z
   static constexpr int nY = d::P3 * YS;            // Y block per (field, level)
+  static constexpr int r32(int x) { return (x + 31) / 32 * 32; }
+  // items of one level group, padded to whole warps so that a warp runs one group
+  static constexpr int GA = r32(EPB * 4 * d::n1);  // a pass: (element, field, a point)
+  // b^T and trace a pass: (element, field, point); at N >= 6 with one element per CTA the
+  // unpadded count (two warps per group) runs faster than whole warps per group
+  static constexpr int GT = (EPB == 1 && N >= 6) ? 4 * d::P3 : r32(EPB * 4 * d::P3);
+  static constexpr int WV = (EPB * d::n2 + 31) / 32;  // warps per mixing half
+  static constexpr int MIXT = 2 * WV * 32;
   // shared-memory layout (floats)
   static constexpr size_t al4(size_t x) { return (x + 3) / 4 * 4; }  // 16-byte alignment
   static constexpr size_t lx = 0;                                // LX copy (nrow x P3)
   static constexpr size_t dl = lx + d::nrow * d::P3;             // DL copy (nrow x n1)
-  // inputs of one element, in two buffers (the next element's arrive by cp.async):
-  // state (4 Np; the new state replaces it), residual (4 Np), geometry (9 n2), face
-  // geometry (NGF), M^{-1} (Np); each part starts on a 16-byte boundary
+  static constexpr size_t dec = dl + d::nrow * d::n1;            // Np mode decodings k | j << 8 | i << 16
+  // inputs of one element: state (4 Np; the new state replaces it), residual (4 Np),
+  // geometry (9 n2), face geometry (NGF), M^{-1} (Np); each part on a 16-byte boundary.
+  // EPB elements form a group; two group buffers (the next group's arrive by cp.async).
   static constexpr size_t bu = 0, bres = al4(4 * d::Np), bgeo = bres + al4(4 * d::Np),
                           bgf = bgeo + al4(d::NGEO * d::n2), binv = bgf + al4(d::NGF), bsz = binv + al4(d::Np);
-  static constexpr size_t buf = al4(dl + d::nrow * d::n1);       // 2 x bsz
-  static constexpr size_t Fs = buf + 2 * bsz;                    // 4 Nfc  [f][g]
-  static constexpr size_t A = Fs + 4 * d::Nfc;                   // [row][p][f]: a pass of u_old (float4 per (row, p))
-  static constexpr size_t dA = A + 4 * d::nrow * d::n1;          // [row][p][f]: a pass, d/da
+  static constexpr size_t buf = al4(dec + d::Np);                // 2 x EPB x bsz
+  static constexpr size_t Fs = buf + 2 * EPB * bsz;              // EPB x 4 Nfc  [f][g]
   static constexpr size_t ZA = 4 * d::nrow * YS > 8 * d::nrow * d::n1 ? 4 * d::nrow * YS : 8 * d::nrow * d::n1;
-  static constexpr size_t Y = A + ZA;                            // 4 n1 nY  [f][k][p'][q']
-  static constexpr size_t dec = Y + 4 * d::n1 * nY;             // Np mode decodings k | j << 8 | i << 16
-  static constexpr size_t total = dec + d::Np;
-  static constexpr size_t Z = A;                                 // 4 nrow YS [f][row][p'] (A, dA dead by then)
+  static constexpr size_t A = Fs + EPB * 4 * d::Nfc;             // EPB x ZA: A, dA as [row][p][f], later Z, At
+  static constexpr size_t Y = A + EPB * ZA;                      // EPB x 4 n1 nY  [f][k][p'][q']
+  static constexpr size_t total = Y + EPB * 4 * d::n1 * nY;
   static_assert(4 * d::nrow * d::P3 <= ZA, "trace a pass (At) aliases the A/dA region");
+  static_assert(MIXT <= NT, "mixing slots");
   // resident CTAs per SM the register budget is tuned for
   static constexpr int MIN_BLOCKS = N <= 5 ? 8 : 4;
   // L2 prefetch of the next element's own and neighbour traces and connectivity: used at
-  // N >= 6, where each element's flux gathers are longest; at lower N its registers push
-  // the kernel into spills
-  static constexpr bool PREFETCH = N >= 6;
+  // N >= 6, where each element's flux gathers are longest
+  static constexpr bool PREFETCH = N >= 6 && EPB == 1;
   static constexpr size_t bytes = total * sizeof(float);
 };
 
-template <int N>
-__global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
+template <int N, int EPB>
+__global__ void __launch_bounds__(128, S32<N, EPB>::MIN_BLOCKS)
     stage32_kernel(int64_t K, float* __restrict__ q, float* __restrict__ res, const float* __restrict__ tr_cur,
-                   float* __restrict__ tr_nxt, const int32_t* __restrict__ mapP, const float* __restrict__ geo,
-                   const float* __restrict__ gface, const float* __restrict__ invM, int bc, float tau, float rka,
-                   float rkb, float dt, const float* __restrict__ dt_elem, int write_traces) {
+                    float* __restrict__ tr_nxt, const int32_t* __restrict__ mapP, const float* __restrict__ geo,
+                    const float* __restrict__ gface, const float* __restrict__ invM, int bc, float tau, float rka,
+                    float rkb, float dt, const float* __restrict__ dt_elem, int write_traces) {
   using d = Dims<N>;
-  using S = S32<N>;
+  using S = S32<N, EPB>;
   using C = C32<N>;
   constexpr int n1 = d::n1, n2 = d::n2, P3 = d::P3, nrow = d::nrow, Np = d::Np, Nfc = d::Nfc;
-  constexpr int YS = S::YS, nY = S::nY;
+  constexpr int YS = S::YS, nY = S::nY, ZA = (int)S::ZA;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
   float* s_lx = sm + S::lx;
   float* s_dl = sm + S::dl;
-  float* s_Fs = sm + S::Fs;
-  float* s_A = sm + S::A;
-  float* s_dA = sm + S::dA;
-  float* s_Y = sm + S::Y;
-  float* s_Z = sm + S::Z;
+  float* s_Fs0 = sm + S::Fs;
+  float* s_A0 = sm + S::A;
+  float* s_Y0 = sm + S::Y;
   int* s_dec = reinterpret_cast<int*>(sm + S::dec);
   const int tid = threadIdx.x;
   for (int n = tid; n < Np; n += S::NT) {
@@ -120,48 +134,58 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
     decode_mode(n, k, j, i);
     s_dec[n] = k | j << 8 | i << 16;
   }
-
   for (int x = tid; x < nrow * P3; x += S::NT) s_lx[x] = c32[C::LX + x];
   for (int x = tid; x < nrow * n1; x += S::NT) s_dl[x] = c32[C::DL + x];
   // Y entries that no pass writes (face rows x face columns) stay zero
-  for (int x = tid; x < 4 * n1 * nY; x += S::NT) s_Y[x] = 0.f;
+  for (int x = tid; x < EPB * 4 * n1 * nY; x += S::NT) s_Y0[x] = 0.f;
 
-  // asynchronous copy of element en's contiguous inputs into buffer block bb. Each
-  // element's blocks start on 16-byte boundaries: 4 Np and NGF = 16 + 4 n2 floats are
-  // multiples of 4; geometry and M^{-1} go by 4-byte copies.
-  auto issue = [&](int64_t en, float* bb) {
-    for (int x = tid; x < Np; x += S::NT) {
-      cp_async16(bb + S::bu + 4 * x, q + en * 4 * Np + 4 * x);
-      cp_async16(bb + S::bres + 4 * x, res + en * 4 * Np + 4 * x);
+  // Element ei of the group starting at e0. Every pass works on all EPB elements, so its
+  // item counts are compile-time constants; past the end of the mesh (the last group)
+  // an element slot holds a copy of element K-1 and only its stores are skipped.
+  auto elem = [&](int64_t e0, int ei) -> int64_t { return e0 + ei < K ? e0 + ei : K - 1; };
+  // asynchronous copy of the group starting at e0 into group buffer bb
+  auto issue = [&](int64_t e0, float* bb) {
+    for (int x = tid; x < EPB * Np; x += S::NT) {
+      const int ei = EPB == 1 ? 0 : x / Np, xx = x - ei * Np;
+      const int64_t ee = elem(e0, ei);
+      cp_async16(bb + ei * S::bsz + S::bu + 4 * xx, q + ee * 4 * Np + 4 * xx);
+      cp_async16(bb + ei * S::bsz + S::bres + 4 * xx, res + ee * 4 * Np + 4 * xx);
     }
-    for (int x = tid; x < d::NGEO * n2; x += S::NT) cp_async4(bb + S::bgeo + x, geo + en * d::NGEO * n2 + x);
-    for (int x = tid; x < d::NGF / 4; x += S::NT) cp_async16(bb + S::bgf + 4 * x, gface + en * d::NGF + 4 * x);
-    for (int x = tid; x < Np; x += S::NT) cp_async4(bb + S::binv + x, invM + en * Np + x);
+    for (int x = tid; x < EPB * d::NGEO * n2; x += S::NT) {
+      const int ei = EPB == 1 ? 0 : x / (d::NGEO * n2), xx = x - ei * (d::NGEO * n2);
+      cp_async4(bb + ei * S::bsz + S::bgeo + xx, geo + elem(e0, ei) * d::NGEO * n2 + xx);
+    }
+    for (int x = tid; x < EPB * (d::NGF / 4); x += S::NT) {
+      const int ei = EPB == 1 ? 0 : x / (d::NGF / 4), xx = x - ei * (d::NGF / 4);
+      cp_async16(bb + ei * S::bsz + S::bgf + 4 * xx, gface + elem(e0, ei) * d::NGF + 4 * xx);
+    }
+    for (int x = tid; x < EPB * Np; x += S::NT) {
+      const int ei = EPB == 1 ? 0 : x / Np, xx = x - ei * Np;
+      cp_async4(bb + ei * S::bsz + S::binv + xx, invM + elem(e0, ei) * Np + xx);
+    }
     cp_async_commit();
   };
-  if ((int64_t)blockIdx.x < K) issue(blockIdx.x, sm + S::buf);
+  const int64_t gstride = (int64_t)gridDim.x * EPB;
+  if ((int64_t)blockIdx.x * EPB < K) issue((int64_t)blockIdx.x * EPB, sm + S::buf);
   int it = 0;
-  for (int64_t e = blockIdx.x; e < K; e += gridDim.x, ++it) {
-    float* bcur = sm + S::buf + (it & 1) * S::bsz;
-    float* s_u = bcur + S::bu;
-    float* s_geo = bcur + S::bgeo;
-    float* s_gf = bcur + S::bgf;
-    const float* s_res = bcur + S::bres;
-    const float* s_inv = bcur + S::binv;
-    cp_async_wait_all();  // this thread's copies of element e have landed
+  for (int64_t e0 = (int64_t)blockIdx.x * EPB; e0 < K; e0 += gstride, ++it) {
+    const int ne = EPB == 1 ? 1 : (int)min((int64_t)EPB, K - e0);  // elements of the group in the mesh
+    float* bcur = sm + S::buf + (it & 1) * EPB * S::bsz;
+    cp_async_wait_all();  // this thread's copies of the group have landed
     __syncthreads();      // ... everyone's; and the other buffer's last reader is done
-    if (e + gridDim.x < K) issue(e + gridDim.x, sm + S::buf + ((it + 1) & 1) * S::bsz);
-    // the next element's traces and connectivity: into L2 while this one computes
-    const int64_t en = e + gridDim.x;
-    if (S::PREFETCH && en < K) {
+    const int64_t en = e0 + gstride;
+    if (en < K) issue(en, sm + S::buf + ((it + 1) & 1) * EPB * S::bsz);
+    if (S::PREFETCH && en < K) {  // the next element's traces and connectivity: into L2
       prefetch_l2(tr_cur + en * Nfc * 4, sizeof(float) * 4 * Nfc, tid, S::NT);
       prefetch_l2(mapP + en * Nfc, sizeof(int32_t) * Nfc, tid, S::NT);
     }
 
     // ---- surface flux at every face point (a4), weighted by w sJ
-    for (int g = tid; g < Nfc; g += S::NT) {
+    for (int x = tid; x < EPB * Nfc; x += S::NT) {
+      const int ei = EPB == 1 ? 0 : x / Nfc, g = x - ei * Nfc;
+      const float* s_gf = bcur + ei * S::bsz + S::bgf;
       const int face = g / n2, idx = g - face * n2;
-      const int64_t gl = e * Nfc + g;
+      const int64_t gl = elem(e0, ei) * Nfc + g;
       const int64_t gn = mapP[gl];
       const float4 a4 = reinterpret_cast<const float4*>(tr_cur)[gl];
       const float4 b4 = reinterpret_cast<const float4*>(tr_cur)[gn];
@@ -171,15 +195,20 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
       const float w = face == 0 ? c32[C::WB + idx] : c32[C::WFT + idx];
       float F[4];
       face_flux<float>(um, up, gn == gl, bc, tau, nv, w * nv[3], F);
+      float* s_Fs = s_Fs0 + ei * 4 * Nfc;
 #pragma unroll
       for (int f = 0; f < 4; ++f) s_Fs[f * Nfc + g] = F[f];
     }
-    // ---- a pass per (level group, field, a point p): A = l^k(a_p) u, dA = l^k'(a_p) u.
-    // Warp g takes levels g and N-g, whose (k+1)^2 costs pair up.
-    if ((tid & 31) < 4 * n1 && (tid >> 5) < S::G) {
-      const int grp = tid >> 5, lane = tid & 31;
-      const int f = lane / n1, p = lane - f * n1;
-      const float* uf = s_u + f * Np;
+    // ---- a pass per (level group, element, field, a point p): A = l^k(a_p) u, dA = l^k'(a_p) u.
+    // Each group's items fill whole warps; group g takes levels g and N-g.
+    for (int x = tid; x < S::G * S::GA; x += S::NT) {
+      const int grp = x / S::GA, r = x - grp * S::GA;
+      if (r >= EPB * 4 * n1) continue;
+      const int ei = EPB == 1 ? 0 : r / (4 * n1), l = r - ei * 4 * n1;
+      const int f = l / n1, p = l - f * n1;
+      const float* uf = bcur + ei * S::bsz + S::bu + f * Np;
+      float* s_A = s_A0 + ei * ZA;
+      float* s_dA = s_A + 4 * nrow * n1;
 #pragma unroll
       for (int k = 0; k <= N; ++k) {
         if (k != grp && k != N - grp) continue;
@@ -206,8 +235,7 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
         }
       }
     }
-    if (S::PREFETCH && e + gridDim.x < K) {  // neighbour traces of the next element (its mapP is in L2 by now)
-      const int64_t en = e + gridDim.x;
+    if (S::PREFETCH && en < K) {  // neighbour traces of the next element (its mapP is in L2 by now)
       for (int g = tid; g < Nfc; g += S::NT) {
         const float* pn = tr_cur + (int64_t)mapP[en * Nfc + g] * 4;
         asm volatile("prefetch.global.L2 [%0];" ::"l"(pn));
@@ -215,18 +243,20 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
     }
     __syncthreads();
 
-    // ---- level mixing (c direction of Alg. 1) per (a,b) point, base lift; triangle-face c^T.
-    // Two warp-aligned halves: the velocity half forms div(u) and feeds the p equation,
-    // the pressure half forms grad(p) and feeds the velocity equations.
-    constexpr int WV = (n2 + 31) / 32;
-    constexpr int MIXT = 2 * WV * 32;
-    static_assert(MIXT <= S::NT, "mixing slots");
-    if (tid < MIXT) {
-      const int half = tid / (WV * 32);
-      const int pq = tid - half * WV * 32;
-      if (pq < n2) {
+    // ---- level mixing (c direction of Alg. 1) per (element, a, b point), base lift;
+    // triangle-face c^T. Two warp-aligned halves: the velocity half forms div(u) and
+    // feeds the p equation, the pressure half forms grad(p) and feeds the velocity equations.
+    if (tid < S::MIXT) {
+      const int half = tid / (S::WV * 32);
+      const int y = tid - half * S::WV * 32;
+      if (y < EPB * n2) {
+        const int ei = EPB == 1 ? 0 : y / n2, pq = y - ei * n2;
         const int p = pq % n1, qq = pq / n1;
-        const float* g = s_geo + pq * d::NGEO;
+        const float* g = bcur + ei * S::bsz + S::bgeo + pq * d::NGEO;
+        const float* s_A = s_A0 + ei * ZA;
+        const float* s_dA = s_A + 4 * nrow * n1;
+        const float* s_Fs = s_Fs0 + ei * 4 * Nfc;
+        float* s_Y = s_Y0 + ei * 4 * n1 * nY;
         if (half == 0) {
           float X[n1], Zc[n1];
 #pragma unroll
@@ -332,36 +362,38 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
         }
       }
     }
-    for (int x = ((tid + S::NT - MIXT) % S::NT) + n2; x < n2 + 16 * n1; x += S::NT) {
-      {
-        const int y = x - n2;
-        const int ee = y % n1;
-        const int slot = (y / n1) % 4;
-        const int f = y / (4 * n1);
-        const int face = slot == 0 ? 1 : slot == 1 ? 3 : slot == 2 ? 4 : 2;
-        const float* fs = s_Fs + f * Nfc + face * n2 + ee;
-        float Fm[n1];
+    for (int x = (tid + S::NT - S::MIXT) % S::NT; x < EPB * 16 * n1; x += S::NT) {
+      const int ei = EPB == 1 ? 0 : x / (16 * n1), y = x - ei * 16 * n1;
+      const int ee = y % n1;
+      const int slot = (y / n1) % 4;
+      const int f = y / (4 * n1);
+      const int face = slot == 0 ? 1 : slot == 1 ? 3 : slot == 2 ? 4 : 2;
+      const float* fs = s_Fs0 + ei * 4 * Nfc + f * Nfc + face * n2 + ee;
+      float Fm[n1];
 #pragma unroll
-        for (int m = 0; m <= N; ++m) Fm[m] = fs[m * n1];
-        float* Yf = s_Y + f * n1 * nY;
+      for (int m = 0; m <= N; ++m) Fm[m] = fs[m * n1];
+      float* Yf = s_Y0 + ei * 4 * n1 * nY + f * n1 * nY;
 #pragma unroll
-        for (int k = 0; k <= N; ++k) {
-          float acc = 0.f;
+      for (int k = 0; k <= N; ++k) {
+        float acc = 0.f;
 #pragma unroll
-          for (int m = 0; m <= N; ++m) acc = fmaf(c32[C::GF + k * n1 + m], Fm[m], acc);
-          if (slot < 2)
-            Yf[k * nY + ee * YS + n1 + slot] = acc;  // b = -1, +1 columns
-          else
-            Yf[k * nY + (n1 + slot - 2) * YS + ee] = acc;  // a = -1, +1 rows
-        }
+        for (int m = 0; m <= N; ++m) acc = fmaf(c32[C::GF + k * n1 + m], Fm[m], acc);
+        if (slot < 2)
+          Yf[k * nY + ee * YS + n1 + slot] = acc;  // b = -1, +1 columns
+        else
+          Yf[k * nY + (n1 + slot - 2) * YS + ee] = acc;  // a = -1, +1 rows
       }
     }
     __syncthreads();
 
     // ---- b^T pass per (field, row p' of Y): Z[f][row(k,j)][p'] = sum_q' l_j^k(x_q') Y[f][k][p'][q']
-    for (int x = tid; x < S::G * 4 * P3; x += S::NT) {
-      const int grp = x / (4 * P3), y = x - grp * 4 * P3;
+    for (int x = tid; x < S::G * S::GT; x += S::NT) {
+      const int grp = x / S::GT, r = x - grp * S::GT;
+      if (r >= EPB * 4 * P3) continue;
+      const int ei = EPB == 1 ? 0 : r / (4 * P3), y = r - ei * 4 * P3;
       const int f = y / P3, pp = y - f * P3;
+      const float* s_Y = s_Y0 + ei * 4 * n1 * nY;
+      float* s_Z = s_A0 + ei * ZA;
 #pragma unroll
       for (int k = 0; k <= N; ++k) {
         if (k != grp && k != N - grp) continue;
@@ -387,12 +419,13 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
     __syncthreads();
 
     // ---- a^T pass, M^{-1} (a6), LSRK update (a7); the new state goes back to shared memory
-    const float dte = dt_elem ? dt_elem[e] : dt;  // per-element step when meshes are batched
-    for (int x = tid; x < 4 * Np; x += S::NT) {
-      const int f = x / Np, n = x - f * Np;
+    const float dte0 = dt_elem ? 0.f : dt;
+    for (int x = tid; x < EPB * 4 * Np; x += S::NT) {
+      const int ei = EPB == 1 ? 0 : x / (4 * Np), xx = x - ei * 4 * Np;
+      const int f = xx / Np, n = xx - f * Np;
       const int kji = s_dec[n];
       const int k = kji & 0xff, j = (kji >> 8) & 0xff, i = kji >> 16;
-      const float* Zr = s_Z + (f * nrow + tri_num(k) + j) * YS;
+      const float* Zr = s_A0 + ei * ZA + (f * nrow + tri_num(k) + j) * YS;
       const float* lr = s_lx + (tri_num(k) + i) * P3;
       float acc = 0.f;
       if (k == N) {  // l_i^N(x_c) = delta_ic on the volume points; the face columns remain
@@ -401,13 +434,18 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
 #pragma unroll
         for (int c = 0; c < P3; ++c) acc = fmaf(lr[c], Zr[c], acc);
       }
-      const float rhs = -s_inv[n] * acc;
-      const int64_t gi = e * 4 * Np + x;
-      const float rnew = fmaf(rka, s_res[x], dte * rhs);
-      res[gi] = rnew;
-      const float unew = fmaf(rkb, rnew, s_u[x]);
-      q[gi] = unew;
-      s_u[x] = unew;
+      float* be = bcur + ei * S::bsz;
+      const float rhs = -be[S::binv + n] * acc;
+      const int64_t ee = elem(e0, ei);
+      const int64_t gi = ee * 4 * Np + xx;
+      const float dte = dt_elem ? dt_elem[ee] : dte0;  // per-element step when meshes are batched
+      const float rnew = fmaf(rka, be[S::bres + xx], dte * rhs);
+      const float unew = fmaf(rkb, rnew, be[S::bu + xx]);
+      be[S::bu + xx] = unew;
+      if (ei < ne) {
+        res[gi] = rnew;
+        q[gi] = unew;
+      }
     }
     if (!write_traces) continue;
     __syncthreads();
@@ -415,11 +453,13 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
     // ---- traces of the updated state (Alg. 3's interpolation to face points) into tr_nxt.
     // First the a direction at every a point and a = -1, +1, by level groups:
     // At[f][row(k,j)][pp] = sum_i u[f][k,j,i] l_i^k(a_pp)   (aliases the dead A/dA/Z region)
-    float* s_At = s_A;
-    for (int x = tid; x < S::G * 4 * P3; x += S::NT) {
-      const int grp = x / (4 * P3), y = x - grp * 4 * P3;
+    for (int x = tid; x < S::G * S::GT; x += S::NT) {
+      const int grp = x / S::GT, r = x - grp * S::GT;
+      if (r >= EPB * 4 * P3) continue;
+      const int ei = EPB == 1 ? 0 : r / (4 * P3), y = r - ei * 4 * P3;
       const int f = y / P3, pp = y - f * P3;
-      const float* uf = s_u + f * Np;
+      const float* uf = bcur + ei * S::bsz + S::bu + f * Np;
+      float* s_At = s_A0 + ei * ZA;
 #pragma unroll
       for (int k = 0; k <= N; ++k) {
         if (k != grp && k != N - grp) continue;
@@ -437,58 +477,60 @@ __global__ void __launch_bounds__(128, S32<N>::MIN_BLOCKS)
       }
     }
     __syncthreads();
-    // then the face points: 16 n1 items for the four triangular faces (a level sum,
-    // then the c direction), 4 n1 items for the base (one a point, all b points)
-    {
-      float* dst = tr_nxt + e * Nfc * 4;
-      for (int x = tid; x < 20 * n1; x += S::NT) {
-        if (x < 16 * n1) {
-          const int f = x & 3, y = x >> 2;
-          const int t = y % n1, kind = y / n1;  // kind: 0 b=-1, 1 b=+1, 2 a=-1, 3 a=+1
-          // faces b = -1, +1 at (a_t, c_m): weights l_j^k(-1 or +1), A column t;
-          // faces a = -1, +1 at (b_t, c_m): weights l_j^k(b_t), A column a = -1 or +1
-          const int wcol = kind < 2 ? n1 + (kind & 1) : t;
-          const int acol = kind < 2 ? t : n1 + (kind & 1);
-          const float* Ar = s_At + f * nrow * P3 + acol;
-          const float* wr = s_lx + wcol;
-          // level N at a volume column t: At is the state itself
-          const float* ArN = kind < 2 ? s_u + f * Np + lvl_off(N) + t : Ar + tri_num(N) * P3;
-          const int sN = kind < 2 ? n1 : P3;
-          float Sk[n1];
+    // then the face points: 16 n1 items per element for the four triangular faces (a level
+    // sum, then the c direction), 4 n1 for the base (one a point, all b points)
+    for (int x = tid; x < EPB * 20 * n1; x += S::NT) {
+      const int ei = EPB == 1 ? 0 : x / (20 * n1), xx = x - ei * 20 * n1;
+      if (ei >= ne) continue;
+      const float* s_At = s_A0 + ei * ZA;
+      const float* s_u = bcur + ei * S::bsz + S::bu;
+      float* dst = tr_nxt + (e0 + ei) * Nfc * 4;
+      if (xx < 16 * n1) {
+        const int f = xx & 3, y = xx >> 2;
+        const int t = y % n1, kind = y / n1;  // kind: 0 b=-1, 1 b=+1, 2 a=-1, 3 a=+1
+        // faces b = -1, +1 at (a_t, c_m): weights l_j^k(-1 or +1), A column t;
+        // faces a = -1, +1 at (b_t, c_m): weights l_j^k(b_t), A column a = -1 or +1
+        const int wcol = kind < 2 ? n1 + (kind & 1) : t;
+        const int acol = kind < 2 ? t : n1 + (kind & 1);
+        const float* Ar = s_At + f * nrow * P3 + acol;
+        const float* wr = s_lx + wcol;
+        // level N at a volume column t: At is the state itself
+        const float* ArN = kind < 2 ? s_u + f * Np + lvl_off(N) + t : Ar + tri_num(N) * P3;
+        const int sN = kind < 2 ? n1 : P3;
+        float Sk[n1];
 #pragma unroll
-          for (int k = 0; k <= N; ++k) {
-            float sacc = 0.f;
+        for (int k = 0; k <= N; ++k) {
+          float sacc = 0.f;
 #pragma unroll
-            for (int j = 0; j <= k; ++j) {
-              const int r = tri_num(k) + j;
-              sacc = fmaf(wr[r * P3], k == N ? ArN[j * sN] : Ar[r * P3], sacc);
-            }
-            Sk[k] = sacc;
+          for (int j = 0; j <= k; ++j) {
+            const int rr = tri_num(k) + j;
+            sacc = fmaf(wr[rr * P3], k == N ? ArN[j * sN] : Ar[rr * P3], sacc);
           }
-          const int face = kind == 0 ? 1 : kind == 1 ? 3 : kind == 2 ? 4 : 2;
+          Sk[k] = sacc;
+        }
+        const int face = kind == 0 ? 1 : kind == 1 ? 3 : kind == 2 ? 4 : 2;
 #pragma unroll
-          for (int m = 0; m <= N; ++m) {
-            float acc = 0.f;
+        for (int m = 0; m <= N; ++m) {
+          float acc = 0.f;
 #pragma unroll
-            for (int k = 0; k <= N; ++k) acc = fmaf(c32[C::GF + k * n1 + m], Sk[k], acc);
-            dst[4 * (face * n2 + t + n1 * m) + f] = acc;
-          }
-        } else {  // base (c = -1) at (a_t, b_c) for every c
-          const int y = x - 16 * n1;
-          const int f = y & 3, t = y >> 2;
-          const float* Ar = s_At + f * nrow * P3 + t;
-          float at[nrow];
+          for (int k = 0; k <= N; ++k) acc = fmaf(c32[C::GF + k * n1 + m], Sk[k], acc);
+          dst[4 * (face * n2 + t + n1 * m) + f] = acc;
+        }
+      } else {  // base (c = -1) at (a_t, b_c) for every c
+        const int y = xx - 16 * n1;
+        const int f = y & 3, t = y >> 2;
+        const float* Ar = s_At + f * nrow * P3 + t;
+        float at[nrow];
 #pragma unroll
-          for (int r = 0; r < tri_num(N); ++r) at[r] = Ar[r * P3];
+        for (int rr = 0; rr < tri_num(N); ++rr) at[rr] = Ar[rr * P3];
 #pragma unroll
-          for (int c = 0; c <= N; ++c) {
-            float acc = 0.f;
+        for (int c = 0; c <= N; ++c) {
+          float acc = 0.f;
 #pragma unroll
-            for (int r = 0; r < tri_num(N); ++r) acc = fmaf(c32[C::CB + r * n1 + c], at[r], acc);
-            // level N: l_j^N(b_c) = delta_jc and At[N][t < n1] is u
-            acc = fmaf(c32[C::GB + N], s_u[f * Np + lvl_off(N) + c * n1 + t], acc);
-            dst[4 * (t + n1 * c) + f] = acc;
-          }
+          for (int rr = 0; rr < tri_num(N); ++rr) acc = fmaf(c32[C::CB + rr * n1 + c], at[rr], acc);
+          // level N: l_j^N(b_c) = delta_jc and At[N][t < n1] is u
+          acc = fmaf(c32[C::GB + N], s_u[f * Np + lvl_off(N) + c * n1 + t], acc);
+          dst[4 * (t + n1 * c) + f] = acc;
         }
       }
     }

@@ -70,6 +70,33 @@ def test_batch_matches_single_mesh_runs_and_oracle(torch_cuda, precision, tol_si
             assert r <= tol_oracle, (i, r)
 
 
+def test_batch_autotuned_elements_per_block(torch_cuda):
+    """Degree groups of at least 4096 pyramids are autotuned at setup over elements per
+    CTA and grid size. Grouping does not change the per-element arithmetic, so each
+    mesh's FP32 state equals the single-mesh run's (which uses the default grouping)."""
+    from paper_1502_07703_gb300.binding import Batch, Solver
+    meshes = []
+    for (nx, ny, nz), n, seed in (((10, 10, 7), 1, 11), ((9, 9, 9), 2, 12), ((1, 2, 1), 3, 13)):
+        v, e = make_pyramid_mesh(nx, ny, nz, delta=0.05, seed=seed)
+        meshes.append((v, e, n))
+    with Batch(meshes, precision="f32") as b:
+        info = {g["N"]: g for g in b.groups()}
+        for g in info.values():
+            assert g["elems_per_block"] in (1, 2, 4, 8)
+            assert 1 <= g["stage_blocks"] <= -(-g["K"] // g["elems_per_block"])
+        dt = b.dt_cfl(0.5)
+        b.project(0.0)
+        b.step(3, dt)
+        states = [b.get_state(i) for i in range(b.nmesh)]
+    for i, (v, e, n) in enumerate(meshes):
+        with Solver(v, e, n, precision="f32") as s:
+            s.project(0.0)
+            s.step(3, dt[i])
+            U = s.get_state()
+        rel = np.linalg.norm(states[i].astype(np.float64) - U) / np.linalg.norm(U.astype(np.float64))
+        assert rel <= 1e-6, (i, rel)
+
+
 def test_batch_oracle_parity_fixed_dt(torch_cuda):
     """Every mesh of a mixed-degree FP64 batch against the oracle over 4 steps."""
     from paper_1502_07703_gb300.binding import Batch

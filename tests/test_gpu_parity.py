@@ -136,6 +136,25 @@ def test_f32_stage_kernel_all_degrees(torch_cuda, N):
     assert rel <= TOL["f32"], rel
 
 
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_f32_stage_kernel_partial_last_group(torch_cuda, N):
+    """At low degree the FP32 stage kernel works on 2 to 8 elements per CTA. A mesh of
+    23 pyramids (one of a 2x2x1-hex mesh dropped: its faces become boundary) leaves the
+    last group partly past the end of the mesh; 5 steps against the oracle."""
+    v, e = make_pyramid_mesh(2, 2, 1, delta=0.1, seed=60 + N)
+    e = e[:-1]
+    dg = PyramidDG(v, e, N)
+    dt = dg.dt_cfl(0.5)
+    U_or = dg.lsrk4(dg.project_exact(0.0), dt, 5)
+    with _solver(v, e, N, precision="f32") as s:
+        assert s.K == 23
+        s.project(0.0)
+        s.step(5, dt)
+        Ug = s.get_state().astype(np.float64)
+    rel = dg.rel_l2_points(dg.values_phi(Ug), dg.values_psi(U_or))
+    assert rel <= TOL["f32"], rel
+
+
 @pytest.mark.parametrize("bc,tau", [("wall", 0.0), ("free", 1.0)])
 def test_f32_stage_kernel_invalidation_and_variants(torch_cuda, bc, tau):
     """Traces stay consistent when stepping is interleaved with rhs (which uses the
