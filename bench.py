@@ -320,7 +320,9 @@ def measure_advection(binding, nx, n, precision, steps, warmup, dev):
     out = {"equation": "advection", "mesh": f"{nx}^3 hexes x 6, periodic", "K": s.K, "N": n, "Np": s.Np,
            "precision": precision, "steps": steps, "ms_per_step": ms / steps,
            "dof_updates_per_s_per_stage": s.K * s.Np * 5 * steps / (ms * 1e-3),
-           "stage_kernel_ms": prof["rhs"][0] / prof["rhs"][1], "trace_kernel_ms": prof["trace"][0] / prof["trace"][1],
+           "stage_kernel_ms": prof["rhs"][0] / prof["rhs"][1],
+           "trace_kernel_ms": prof["trace"][0] / prof["trace"][1] if prof["trace"][1] else 0.0,
+           "launches_per_step": (prof["rhs"][1] + prof["trace"][1]) / steps,
            "l2_rel_error_vs_exact": s.error()[1]}
     s.close()
     return out

@@ -98,6 +98,28 @@ void free_all(pyr_dg* h) {
 
 namespace pyrdg {
 int enqueue_steps(pyr_dg* h, int nsteps, double dt) {
+  if (h->equation == PYR_DG_ADVECTION && h->use_stage32 && nsteps > 0) {
+    // FP32 advection: one launch per stage; traces ping-pong between tr and tr2
+    void* buf[2] = {h->tr, h->tr2};
+    size_t slot = 0;
+    if (!h->tr_valid) {
+      CUDA_TRY(prof_begin(h, 0, &slot));
+      h->L->trace1(h->K, h->q, h->tab, buf[h->tr_cur], h->stream);
+      CUDA_TRY(prof_end(h, slot));
+    }
+    for (int n = 0; n < nsteps; ++n) {
+      for (int s = 0; s < 5; ++s) {
+        CUDA_TRY(prof_begin(h, 1, &slot));
+        h->L->adv32(h->K, h->q, h->res, buf[h->tr_cur], buf[1 - h->tr_cur], h->mapP, h->geo, h->gface, h->invM,
+                    h->beta, h->tau, kRkA[s], kRkB[s], dt, h->stage_epb, h->stage_blocks, h->stream);
+        CUDA_TRY(prof_end(h, slot));
+        h->tr_cur = 1 - h->tr_cur;
+      }
+    }
+    CUDA_TRY(cudaGetLastError());
+    h->tr_valid = true;
+    return PYR_DG_OK;
+  }
   if (h->equation == PYR_DG_ADVECTION) {
     for (int n = 0; n < nsteps; ++n) {
       for (int s = 0; s < 5; ++s) {
@@ -301,7 +323,8 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   h->err_blocks = (int)std::min<int64_t>(K, (int64_t)(nsm > 0 ? nsm : 1) * 4);
 
   const size_t ts = h->tsize;
-  h->use_stage32 = h->L->stage32 != nullptr && h->equation == PYR_DG_WAVE;
+  // FP32 handles take the single-launch stage kernels (wave or advection)
+  h->use_stage32 = h->L->stage32 != nullptr;
   const size_t stateB = (size_t)K * h->nf * Np * ts;
   const pyrdg::TabLayout TL(N);
   struct Alloc {
@@ -343,9 +366,11 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   if (e == cudaSuccess) e = h->L->prepare();
   if (e == cudaSuccess && h->use_stage32) {
     e = h->L->upload_c32(T.tab.data());
-    h->stage_epb = h->L->epb32;
+    const bool adv = h->equation == PYR_DG_ADVECTION;
+    h->stage_epb = adv ? h->L->epb_adv32 : h->L->epb32;
+    const int bps = adv ? h->L->blocks_per_sm_adv32(h->stage_epb) : h->L->blocks_per_sm32(h->stage_epb);
     const int64_t groups = (K + h->stage_epb - 1) / h->stage_epb;
-    h->stage_blocks = (int)std::min<int64_t>(groups, (int64_t)(nsm > 0 ? nsm : 1) * h->L->blocks_per_sm32(h->stage_epb));
+    h->stage_blocks = (int)std::min<int64_t>(groups, (int64_t)(nsm > 0 ? nsm : 1) * bps);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->tab, tabsrc, (size_t)TL.size * ts, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->tabd, T.tab.data(), (size_t)TL.size * 8, cudaMemcpyHostToDevice, s);

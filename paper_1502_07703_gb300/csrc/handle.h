@@ -21,7 +21,7 @@ struct pyr_dg {
   int nf = 4;                  // fields per element in the state
   double beta[3] = {1.0, 0.0, 0.0};
   double box_lo = 0.0, box_hi = 1.0;
-  bool use_stage32 = false;    // FP32 wave handle: single-launch stage kernel
+  bool use_stage32 = false;    // FP32 handle: single-launch stage kernel (wave or advection)
   double tau = 1.0;
   int64_t K = 0;
   size_t tsize = 8;

@@ -2,6 +2,7 @@
 #pragma once
 #include "dg_kernels.cuh"
 #include "stage32.cuh"
+#include "adv32.cuh"
 #include "adv_kernels.cuh"
 #include "launch.h"
 
@@ -136,6 +137,59 @@ struct Impl {
 #undef PYRDG_STAGE32_ARGS
   }
   template <int E>
+  static void adv32_e(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
+                      const void* geo, const void* gface, const void* invM, const double* beta, double alpha,
+                      double rka, double rkb, double dt, int nblocks, cudaStream_t s) {
+    if constexpr (epb1_supported(N, E)) {
+      static_assert(A32<N, E>::bytes <= kMaxSmem, "FP32 advection kernel shared memory");
+      adv32_kernel<N, E><<<nblocks, A32<N, E>::NT, A32<N, E>::bytes, s>>>(
+          K, (float*)q, (float*)res, (const float*)tr_cur, (float*)tr_nxt, mapP, (const float*)geo,
+          (const float*)gface, (const float*)invM, (float)beta[0], (float)beta[1], (float)beta[2], (float)alpha,
+          (float)rka, (float)rkb, (float)dt);
+    }
+  }
+  // epb must be one blocks_per_sm_adv32 reports as built (nonzero)
+  static void adv32(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
+                    const void* geo, const void* gface, const void* invM, const double* beta, double alpha,
+                    double rka, double rkb, double dt, int epb, int nblocks, cudaStream_t s) {
+#define PYRDG_ADV32_ARGS K, q, res, tr_cur, tr_nxt, mapP, geo, gface, invM, beta, alpha, rka, rkb, dt, nblocks, s
+    switch (epb) {
+      case 2: adv32_e<2>(PYRDG_ADV32_ARGS); break;
+      case 4: adv32_e<4>(PYRDG_ADV32_ARGS); break;
+      case 8: adv32_e<8>(PYRDG_ADV32_ARGS); break;
+      default: adv32_e<1>(PYRDG_ADV32_ARGS); break;
+    }
+#undef PYRDG_ADV32_ARGS
+  }
+  template <int E>
+  static cudaError_t smem_adv32() {
+    if constexpr (epb1_supported(N, E))
+      return cudaFuncSetAttribute(adv32_kernel<N, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)A32<N, E>::bytes);
+    return cudaSuccess;
+  }
+  template <int E>
+  static int bps_adv32() {
+    if constexpr (epb1_supported(N, E)) {
+      int n = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adv32_kernel<N, E>, A32<N, E>::NT,
+                                                        A32<N, E>::bytes) != cudaSuccess)
+        return 1;
+      return n > 0 ? n : 1;
+    }
+    return 0;
+  }
+  // Resident CTAs per SM of the advection stage kernel with epb elements per CTA; 0 if not built.
+  static int blocks_per_sm_adv32(int epb) {
+    switch (epb) {
+      case 1: return bps_adv32<1>();
+      case 2: return bps_adv32<2>();
+      case 4: return bps_adv32<4>();
+      case 8: return bps_adv32<8>();
+      default: return 0;
+    }
+  }
+  template <int E>
   static cudaError_t smem32() {
     if constexpr (epb_supported(N, E))
       return cudaFuncSetAttribute(stage32_kernel<N, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -177,6 +231,10 @@ struct Impl {
     if (e == cudaSuccess) e = smem32<2>();
     if (e == cudaSuccess) e = smem32<4>();
     if (e == cudaSuccess) e = smem32<8>();
+    if (e == cudaSuccess) e = smem_adv32<1>();
+    if (e == cudaSuccess) e = smem_adv32<2>();
+    if (e == cudaSuccess) e = smem_adv32<4>();
+    if (e == cudaSuccess) e = smem_adv32<8>();
     return e;
   }
   // Resident CTAs per SM of the stage kernel with epb elements per CTA; 0 if not built.
@@ -213,12 +271,19 @@ struct Impl {
       l.blocks_per_sm32 = &blocks_per_sm32;
       // measured best on 196,608 pyramids: groups of 8 at N = 1, 2 at N = 2, 3, else 1
       l.epb32 = N == 1 ? 8 : N <= 3 ? 2 : 1;
+      l.adv32 = &adv32;
+      l.blocks_per_sm_adv32 = &blocks_per_sm_adv32;
+      // one field leaves more of the CTA idle per element than the wave system
+      l.epb_adv32 = N <= 2 ? 8 : N <= 4 ? 4 : 2;
       l.smem_stage32 = S32<N, 1>::bytes;
     } else {
       l.stage32 = nullptr;
       l.upload_c32 = nullptr;
       l.blocks_per_sm32 = nullptr;
       l.epb32 = 1;
+      l.adv32 = nullptr;
+      l.blocks_per_sm_adv32 = nullptr;
+      l.epb_adv32 = 1;
       l.smem_stage32 = 0;
     }
     return l;

@@ -36,6 +36,13 @@ struct Launchers {
   // persistent grid); 0 when that epb is not built for this degree.
   int (*blocks_per_sm32)(int epb);
   int epb32;  // default elements per CTA of the FP32 stage kernel
+  // Single-launch FP32 advection stage (null for double): reads the traces of q from
+  // tr_cur and writes the updated state, residual and the new traces into tr_nxt.
+  void (*adv32)(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
+                const void* geo, const void* gface, const void* invM, const double* beta, double alpha, double rka,
+                double rkb, double dt, int epb, int nblocks, cudaStream_t s);
+  int (*blocks_per_sm_adv32)(int epb);
+  int epb_adv32;  // default elements per CTA of the FP32 advection stage kernel
   size_t smem_stage32;
   // Scalar advection (one field): trace, fused stage / rhs, projection and error norm.
   void (*trace1)(int64_t K, const void* q, const void* tab, void* tr, cudaStream_t s);

@@ -66,3 +66,24 @@ def test_advection_evolution_projection_and_error(torch_cuda, precision):
     assert rel <= TOL[precision], rel
     eo = ad.error(U10, 10 * dt)
     np.testing.assert_allclose(err, eo, rtol=1e-9 if precision == "f64" else 1e-3)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
+def test_advection_f32_stage_kernel_all_degrees(torch_cuda, N):
+    """The single-launch FP32 advection kernel (several elements per CTA, ping-pong
+    traces) at every degree: 6 steps from the projected field, taken in calls of 1, 2
+    and 3 steps, against the oracle. 3x3x1 hexes give 54 pyramids, so with 4 or 8
+    elements per CTA the last group runs past the end of the mesh."""
+    v, e = make_pyramid_mesh(3, 3, 1, delta=0.1, seed=70 + N)
+    ad = PyramidAdvection(v, e, N, beta=BETA)
+    dt = ad.dt_cfl(0.5)
+    U6 = ad.lsrk4(ad.project_exact(0.0), dt, 6)
+    with _solver(v, e, N, precision="f32") as s:
+        assert s.K == 54
+        s.project(0.0)
+        s.step(1, dt)
+        s.step(2, dt)
+        s.step(3, dt)
+        G = s.get_state().astype(np.float64)
+    rel = ad.dg.rel_l2_points(ad.dg.values_phi(G), ad.dg.values_psi(U6))
+    assert rel <= TOL["f32"], rel
