@@ -185,7 +185,9 @@ int pyr_dg_profile(pyr_dg* h, int enable);
 
 /* Totals since the last pyr_dg_profile call: device milliseconds and launch
  * counts of the trace kernel and of the fused volume/flux/lift/M^{-1}/update
- * kernel. Synchronises the stream. Any pointer may be NULL. */
+ * kernel. FP32 handles run one stage kernel that also writes the new state's
+ * traces; their trace kernel runs only when the traces are not current (after
+ * setup, set_state, project or rhs). Synchronises the stream. Any pointer may be NULL. */
 int pyr_dg_profile_read(pyr_dg* h, double* trace_ms, int64_t* trace_launches, double* rhs_ms,
                         int64_t* rhs_launches);
 

@@ -22,7 +22,7 @@
 
 namespace pyrdg {
 
-// Constant-memory table layout of the FP32 stage kernel for degree N.
+// Constant-memory table layout of the FP32 stage kernels (wave and advection) for degree N.
 template <int N>
 struct C32 {
   using d = Dims<N>;
@@ -51,6 +51,8 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, int tid
     asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
 }
 
+// Asynchronous global -> shared copies (cp.async): 16 bytes (both addresses 16-byte
+// aligned) or 4 bytes; a commit closes the group, wait_all waits for this thread's groups.
 __device__ __forceinline__ void cp_async16(void* s, const void* g) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g));
 }
