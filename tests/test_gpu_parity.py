@@ -261,3 +261,46 @@ def test_full_size_config2_sampled(torch_cuda):
         Up = dg.lsrk4(dg.project_exact(0.0), dt_or, 1)
         rel = dg.rel_l2_points(dg.values_phi(U1[patch])[i:i + 1], dg.values_psi(Up)[i:i + 1])
         assert rel <= TOL["f64"], (c, rel)
+
+
+def test_full_size_config5_f32_sampled(torch_cuda):
+    """Config of the large run: 64^3 hexes x 6 = 1,572,864 pyramids, +-0.1h (seed 3), N = 5,
+    FP32, through the single-launch stage kernel as the bench launches it. One LSRK4 step
+    from the projected standing wave, checked on sampled elements whose 6-hop
+    neighbourhood the oracle advances."""
+    v, e = make_pyramid_mesh(64, delta=0.1, seed=3)
+    K, N = e.shape[0], 5
+    assert K == 1572864
+    nbrs = _face_neighbours(e)
+    rng = np.random.default_rng(13)
+    samples = [int(x) for x in rng.choice(K, 2, replace=False)] + [K - 1]
+    dt_or = PyramidDG(v, e[:6], N).dt_cfl(0.5)
+    with _solver(v, e, N, precision="f32") as s:
+        s.project(0.0)
+        s.step(1, dt_or)
+        U1 = s.get_state().astype(np.float64)
+    for c in samples:
+        patch = _patch(nbrs, c, 6)
+        dg = PyramidDG(v, e[patch], N)
+        i = patch.index(c)
+        Up = dg.lsrk4(dg.project_exact(0.0), dt_or, 1)
+        rel = dg.rel_l2_points(dg.values_phi(U1[patch])[i:i + 1], dg.values_psi(Up)[i:i + 1])
+        assert rel <= TOL["f32"], (c, rel)
+
+
+@pytest.mark.parametrize("N", [1, 2, 5])
+def test_f32_stage_kernel_single_element(torch_cuda, N):
+    """One pyramid, all faces on the wall: with several elements per CTA the only group
+    is one element and copies of it (stores skipped); 4 steps against the oracle."""
+    v, e = make_pyramid_mesh(1, delta=0.0)
+    e = e[:1]
+    dg = PyramidDG(v, e, N)
+    dt = dg.dt_cfl(0.5)
+    U_or = dg.lsrk4(dg.project_exact(0.0), dt, 4)
+    with _solver(v, e, N, precision="f32") as s:
+        assert s.K == 1
+        s.project(0.0)
+        s.step(4, dt)
+        Ug = s.get_state().astype(np.float64)
+    rel = dg.rel_l2_points(dg.values_phi(Ug), dg.values_psi(U_or))
+    assert rel <= TOL["f32"], rel

@@ -129,3 +129,19 @@ def test_advection_setup_requires_periodic_box():
     v, e = make_pyramid_mesh(1)
     with pytest.raises(binding.PyrDGError, match="BAD_ARG"):
         binding.Solver(v, e, 2, equation="advection")
+
+
+def test_setup_rejects_empty_and_degenerate_meshes():
+    v, e = make_pyramid_mesh(1, delta=0.0)
+    with pytest.raises(binding.PyrDGError, match="BAD_ARG"):
+        binding.Solver(v, e[:0], 2)                # no elements
+    with pytest.raises(binding.PyrDGError, match="BAD_ARG"):
+        binding.Solver(v[:4], e[:0], 2)            # fewer than 5 vertices
+    flat = e.copy()
+    flat[:, 4] = flat[:, 0]                        # apex on a base vertex: J = 0
+    with pytest.raises(binding.PyrDGError, match="BAD_MESH"):
+        binding.Solver(v, flat, 2)
+    bad = e.copy()
+    bad[0, 2] = v.shape[0]                         # vertex index out of range
+    with pytest.raises(binding.PyrDGError, match="BAD"):
+        binding.Solver(v, bad, 2)
