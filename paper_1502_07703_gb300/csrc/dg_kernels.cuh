@@ -77,18 +77,34 @@ __device__ __forceinline__ double d_jacobian(const double* v, double a, double b
 // Exact standing waves (wall on [0,1]^3, free surface on [-1,1]^3). The spatial
 // factors are cos/sin(pi s x) with s = 1 (wall) or 1/2 (free), evaluated with
 // sincospi; ct, st = cos, sin(sqrt(3) pi s t) come from the caller once per launch.
+// The exact fields from the sines and cosines s[m], c[m] of pi sc x_m.
+__device__ __forceinline__ void d_exact_sc(const double* s, const double* c, double ct, double st, double* out) {
+  const double inv_s3 = 0.57735026918962576451;
+  const double cyz = c[1] * c[2];
+  out[0] = c[0] * cyz * ct;
+  out[1] = s[0] * cyz * (st * inv_s3);
+  out[2] = c[0] * s[1] * c[2] * (st * inv_s3);
+  out[3] = c[0] * c[1] * s[2] * (st * inv_s3);
+}
+
 __device__ __forceinline__ void d_exact(int bc, double x, double y, double z, double ct, double st, double* out) {
   const double sc = bc == 0 ? 1.0 : 0.5;
-  const double inv_s3 = 0.57735026918962576451;
-  double sx, cx, sy, cy, sz, cz;
-  sincospi(sc * x, &sx, &cx);
-  sincospi(sc * y, &sy, &cy);
-  sincospi(sc * z, &sz, &cz);
-  const double cyz = cy * cz;
-  out[0] = cx * cyz * ct;
-  out[1] = sx * cyz * (st * inv_s3);
-  out[2] = cx * sy * cz * (st * inv_s3);
-  out[3] = cx * cy * sz * (st * inv_s3);
+  double s[3], c[3];
+  sincospi(sc * x, &s[0], &c[0]);
+  sincospi(sc * y, &s[1], &c[1]);
+  sincospi(sc * z, &s[2], &c[2]);
+  d_exact_sc(s, c, ct, st, out);
+}
+
+// sin(alpha + eps), cos(alpha + eps) from sin, cos of alpha and a small eps, |eps| <= 0.1,
+// by the angle-addition formulas with the Taylor series of sin(eps) and cos(eps) to
+// eps^9 and eps^8 (the first omitted terms are below 3e-17 for |eps| <= 0.1).
+__device__ __forceinline__ void d_sincos_shift(double sa, double ca, double eps, double* s, double* c) {
+  const double e2 = eps * eps;
+  const double ce = 1.0 + e2 * (-1.0 / 2 + e2 * (1.0 / 24 + e2 * (-1.0 / 720 + e2 * (1.0 / 40320))));
+  const double se = eps * (1.0 + e2 * (-1.0 / 6 + e2 * (1.0 / 120 + e2 * (-1.0 / 5040 + e2 * (1.0 / 362880)))));
+  *s = sa * ce + ca * se;
+  *c = ca * ce - sa * se;
 }
 
 __device__ __forceinline__ void d_time_factors(int bc, double t, double* ct, double* st) {
@@ -767,7 +783,10 @@ struct ErrSmem {
   static constexpr size_t LQ = B + 4 * d::n1 * Q * Q;
   static constexpr size_t GQ = LQ + d::nrow * Q;
   static constexpr size_t XB = GQ + d::n1 * Q;  // per (a,b) point: B(a,b) and w_p w_q J(a,b)
-  static constexpr size_t total = XB + 4 * Q * Q;
+  // per (a,b) point and coordinate m: sin, cos of pi sc alpha_m and pi sc beta_m, where
+  // x_m(c) = alpha_m + beta_m c along the c line through (a, b)
+  static constexpr size_t TS = XB + 4 * Q * Q;
+  static constexpr size_t total = TS + 9 * Q * Q;
   static constexpr size_t bytes = total * sizeof(double);
 };
 
@@ -788,6 +807,7 @@ __global__ void __launch_bounds__(ErrCfg<N>::NT)
   double* s_LQ = sm + S::LQ;
   double* s_GQ = sm + S::GQ;
   double* s_XB = sm + S::XB;
+  double* s_TS = sm + S::TS;
   __shared__ double v[15];
   __shared__ double red[2][NW];
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -796,6 +816,7 @@ __global__ void __launch_bounds__(ErrCfg<N>::NT)
   double e2 = 0.0, n2 = 0.0;
   double ct, st;
   d_time_factors(bc, t, &ct, &st);
+  const double sc = bc == 0 ? 1.0 : 0.5;  // the exact fields are trigonometric in pi sc x
   for (int64_t e = blockIdx.x; e < K; e += gridDim.x) {
     __syncthreads();
     for (int x = tid; x < 4 * d::Np; x += nthr) s_u[x] = (double)q[e * 4 * d::Np + x];
@@ -811,6 +832,11 @@ __global__ void __launch_bounds__(ErrCfg<N>::NT)
       s_XB[4 * x + 1] = B[1];
       s_XB[4 * x + 2] = B[2];
       s_XB[4 * x + 3] = gtab[G.WQ + p] * gtab[G.WQ + qq] * (Ba[0] * g1[0] + Ba[1] * g1[1] + Ba[2] * g1[2]);
+      for (int m = 0; m < 3; ++m) {
+        const double alpha = 0.5 * (B[m] + v[12 + m]);
+        sincospi(sc * alpha, &s_TS[9 * x + m], &s_TS[9 * x + 3 + m]);
+        s_TS[9 * x + 6 + m] = 3.14159265358979323846 * sc * D[m];  // pi sc beta_m (beta = (v5 - B)/2 = D)
+      }
     }
     for (int x = tid; x < 4 * d::nrow * Q; x += nthr) {  // a pass, level-major
       int k = 0;
@@ -842,9 +868,19 @@ __global__ void __launch_bounds__(ErrCfg<N>::NT)
       const int pq = x % (Q * Q), r = x / (Q * Q);
       const double c = gtab[G.XQC + r];
       const double* xb = s_XB + 4 * pq;
-      double Ue[4];
-      d_exact(bc, 0.5 * (1 - c) * xb[0] + 0.5 * (1 + c) * v[12], 0.5 * (1 - c) * xb[1] + 0.5 * (1 + c) * v[13],
-              0.5 * (1 - c) * xb[2] + 0.5 * (1 + c) * v[14], ct, st, Ue);
+      const double* ts = s_TS + 9 * pq;
+      double sn[3], cs[3], Ue[4];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        // pi sc x_m = pi sc alpha_m + eps with eps = pi sc beta_m c: on fine meshes eps is small
+        // and one angle addition replaces the sincospi of every point
+        const double eps = ts[6 + m] * c;
+        if (fabs(eps) <= 0.1)
+          d_sincos_shift(ts[m], ts[3 + m], eps, &sn[m], &cs[m]);
+        else
+          sincospi(sc * (0.5 * (1 - c) * xb[m] + 0.5 * (1 + c) * v[12 + m]), &sn[m], &cs[m]);
+      }
+      d_exact_sc(sn, cs, ct, st, Ue);
       const double w = xb[3] * gtab[G.WQC + r];
 #pragma unroll
       for (int f = 0; f < 4; ++f) {

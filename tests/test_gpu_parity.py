@@ -304,3 +304,20 @@ def test_f32_stage_kernel_single_element(torch_cuda, N):
         Ug = s.get_state().astype(np.float64)
     rel = dg.rel_l2_points(dg.values_phi(Ug), dg.values_psi(U_or))
     assert rel <= TOL["f32"], rel
+
+
+@pytest.mark.parametrize("nx,bc", [(8, "wall"), (16, "wall"), (16, "free")])
+def test_error_norm_fine_meshes(torch_cuda, nx, bc):
+    """The FP64 error norm of a random state at t = 0.3 against the oracle's. On fine meshes
+    the kernel evaluates the exact fields along each c line by angle addition from the
+    (a, b) point (16^3 hexes: everywhere; 8^3: at some points), elsewhere with sincospi."""
+    from oracle.dg import PyramidDG as DG
+    v, e = make_pyramid_mesh(nx, delta=0.05, seed=5, domain=_domain(bc))
+    N = 2
+    dg = DG(v, e, N, bc=bc)
+    U = random_state(dg.K, dg.Np, 21)
+    with _solver(v, e, N, bc=bc) as s:
+        s.set_state(U, t=0.3)
+        err_gpu = s.error()
+    err_or = dg.error(dg.psi_from_phi(U), 0.3)
+    np.testing.assert_allclose(err_gpu, err_or, rtol=1e-12)
