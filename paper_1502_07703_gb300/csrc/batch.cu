@@ -3,8 +3,9 @@
 // face is shared across meshes), so each RK stage is one persistent launch per
 // degree over all of them; each element carries its own mesh's time step. A
 // whole batch step is captured once as a CUDA graph and replayed. For FP32
-// batches the persistent grid of each degree is autotuned at setup by timing
-// candidate grids on the (all-zero) initial state, which leaves it unchanged.
+// batches the elements per CTA and the persistent grid of each degree are
+// autotuned at setup by timing candidates on the (all-zero) initial state, which
+// leaves it unchanged.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,15 +50,18 @@ void destroy_batch(pyr_dg_batch* b) {
   delete b;
 }
 
-// Time one step of a handle with the given persistent grid (state must be all zero
-// and dt_elem zero, so the step leaves it zero).
+// Time one step of a handle with the given elements per CTA and persistent grid (state
+// must be all zero and dt_elem zero, so the step leaves it zero).
 int time_grid(pyr_dg* h, int epb, int blocks, float* ms) {
   h->stage_epb = epb;
   h->stage_blocks = blocks;
   h->tr_valid = false;
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
-  CUDA_TRY(cudaEventCreate(&e1));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(PYR_DG_ERR_CUDA, "autotune: cannot create an event");
+  }
   int rc = pyrdg::enqueue_steps(h, 1, 1.0);  // warm
   if (rc == PYR_DG_OK) {
     cudaEventRecord(e0, h->stream);
