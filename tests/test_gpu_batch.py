@@ -97,6 +97,27 @@ def test_batch_autotuned_elements_per_block(torch_cuda):
         assert rel <= 1e-6, (i, rel)
 
 
+@pytest.mark.parametrize("precision,tol", [("f32", 1e-5), ("f64", 1e-12)])
+def test_batch_lowest_and_highest_degrees(torch_cuda, precision, tol):
+    """A batch of N = 1, 6 and 7 meshes (FP32: 8 elements per CTA at N = 1, one at 6 and 7)
+    against the oracle after 3 steps of each mesh's own dt."""
+    from paper_1502_07703_gb300.binding import Batch
+    meshes = []
+    for (nx, ny, nz), n, seed in (((3, 1, 1), 1, 21), ((1, 2, 1), 6, 22), ((1, 1, 1), 7, 23)):
+        v, e = make_pyramid_mesh(nx, ny, nz, delta=0.08, seed=seed)
+        meshes.append((v, e, n))
+    with Batch(meshes, precision=precision) as b:
+        dt = b.dt_cfl(0.5)
+        b.project(0.0)
+        b.step(3, dt)
+        states = [b.get_state(i).astype(np.float64) for i in range(b.nmesh)]
+    for i, (v, e, n) in enumerate(meshes):
+        dg = PyramidDG(v, e, n)
+        Ur = dg.lsrk4(dg.project_exact(0.0), dt[i], 3)
+        r = dg.rel_l2_points(dg.values_phi(states[i]), dg.values_psi(Ur))
+        assert r <= tol, (n, r)
+
+
 def test_batch_oracle_parity_fixed_dt(torch_cuda):
     """Every mesh of a mixed-degree FP64 batch against the oracle over 4 steps."""
     from paper_1502_07703_gb300.binding import Batch
