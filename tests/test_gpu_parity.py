@@ -321,3 +321,25 @@ def test_error_norm_fine_meshes(torch_cuda, nx, bc):
         err_gpu = s.error()
     err_or = dg.error(dg.psi_from_phi(U), 0.3)
     np.testing.assert_allclose(err_gpu, err_or, rtol=1e-12)
+
+
+@pytest.mark.parametrize("nx,N", [(32, 5), (16, 7)])
+def test_config3_f32_200_steps_against_f64(torch_cuda, nx, N):
+    """Config 3 (the precision form): 200 LSRK4 steps from the projected standing wave
+    in FP32 (single-launch stage kernel) and in FP64. The FP64 path matches the oracle
+    to 1e-12 (tests above), so it stands in for the oracle at this size; the FP32
+    coefficients must agree with it to the FP32 tolerance in relative L2, and both must be
+    close to the exact solution."""
+    from paper_1502_07703_gb300.binding import Solver
+    v, e = make_pyramid_mesh(nx, delta=0.05, seed=1)
+    states, errs = {}, {}
+    for prec in ("f64", "f32"):
+        with Solver(v, e, N, precision=prec) as s:
+            dt = s.dt_cfl(0.5) if prec == "f64" else dt
+            s.project(0.0)
+            s.step(200, dt)
+            states[prec] = s.get_state().astype(np.float64)
+            errs[prec] = s.error()[1]
+    rel = np.linalg.norm(states["f32"] - states["f64"]) / np.linalg.norm(states["f64"])
+    assert rel <= TOL["f32"], rel
+    assert errs["f64"] < 1e-6 and errs["f32"] < 1e-5, errs
