@@ -103,8 +103,9 @@ struct S32 {
   static constexpr size_t total = Y + EPB * 4 * d::n1 * nY;
   static_assert(4 * d::nrow * d::P3 <= ZA, "trace a pass (At) aliases the A/dA region");
   static_assert(MIXT <= NT, "mixing slots");
-  // resident CTAs per SM the register budget is tuned for
-  static constexpr int MIN_BLOCKS = N <= 5 ? 8 : 4;
+  // resident CTAs per SM the register budget is tuned for (at N = 6, 5 CTAs with 96
+  // registers run faster than 4 with 127; N = 7 is held to 4 by shared memory)
+  static constexpr int MIN_BLOCKS = N <= 5 ? 8 : 5;
   // L2 prefetch of the next element's own and neighbour traces and connectivity: used at
   // N >= 6, where each element's flux gathers are longest
   static constexpr bool PREFETCH = N >= 6 && EPB == 1;
