@@ -418,6 +418,9 @@ def main():
     ap.add_argument("--degree", type=int, default=N, help="polynomial degree (4 = the benchmark workload)")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"],
                     help="f64 = the benchmark workload; f32 = the precision form (for profiling runs)")
+    ap.add_argument("--batch", action="store_true",
+                    help="only time the batching form (256 meshes, N = 2..6, FP32) and print it as JSON "
+                         "(for profiling runs)")
     ap.add_argument("--equation", default="wave", choices=["wave", "advection"],
                     help="advection: only time the scalar advection workload (Sec. 4.1) on a periodic "
                          "nx^3 box at --degree and --precision and print that as JSON (for profiling runs)")
@@ -438,6 +441,10 @@ def main():
     dev = local if torch.cuda.is_available() else 0
     torch.cuda.set_device(dev)
     device = torch.device("cuda", dev)
+    if args.batch:
+        if rank == 0:
+            print(json.dumps(measure_batch(binding, args.steps, args.warmup, dev)), flush=True)
+        return
     if args.equation == "advection":
         if rank == 0:
             print(json.dumps(measure_advection(binding, args.nx, args.degree, args.precision, args.steps,

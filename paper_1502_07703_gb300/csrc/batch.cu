@@ -182,20 +182,18 @@ int pyr_dg_batch_setup(int nmesh, const double* const* vertices, const int64_t* 
       return fail(PYR_DG_ERR_NO_MEMORY, "cannot allocate the per-element time steps");
     }
     // Autotune the FP32 stage kernel on the zero state: elements per CTA (1, 2, 4, 8 where
-    // built for this degree) and the persistent grid (1..16 resident-CTA waves per SM).
+    // built for this degree) and the persistent grid (1 .. resident CTAs per SM, per SM).
     if (h->use_stage32 && h->K >= 4096) {
       int nsm = 1;
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
       int best_epb = h->stage_epb, best = h->stage_blocks;
       float best_ms = 1e30f;
       const int epbs[] = {1, 2, 4, 8};
-      const int mult[] = {1, 2, 3, 4, 6, 8, 12, 16};
       for (int epb : epbs) {
         const int bps = h->L->blocks_per_sm32(epb);
         if (bps <= 0) continue;
         const int64_t groups = (h->K + epb - 1) / epb;
-        for (int m : mult) {
-          if (m > bps) break;
+        for (int m = 1; m <= bps; ++m) {
           const int blocks = (int)std::min<int64_t>(groups, (int64_t)m * nsm);
           float ms = 0.f;
           const int trc = time_grid(h, epb, blocks, &ms);
