@@ -63,6 +63,7 @@ _SIGNATURES = {
     "pyr_dg_rhs": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_void_p]),
     "pyr_dg_step": (ctypes.c_int, [_c_h, ctypes.c_int, ctypes.c_double]),
     "pyr_dg_error": (ctypes.c_int, [_c_h, _c_dp, _c_dp]),
+    "pyr_dg_set_error_cache": (ctypes.c_int, [_c_h, ctypes.c_int]),
     "pyr_dg_dt_cfl": (ctypes.c_int, [_c_h, ctypes.c_double, _c_dp]),
     "pyr_dg_time": (ctypes.c_int, [_c_h, _c_dp]),
     "pyr_dg_sync": (ctypes.c_int, [_c_h]),
@@ -276,6 +277,11 @@ class Solver:
         a, r = ctypes.c_double(), ctypes.c_double()
         _check(lib().pyr_dg_error(self._h, ctypes.byref(a), ctypes.byref(r)))
         return a.value, r.value
+
+    def set_error_cache(self, enable=True):
+        """Store the exact fields' spatial factors for error() when they fit (the default),
+        or evaluate them at every call (enable=False)."""
+        _check(lib().pyr_dg_set_error_cache(self._h, 1 if enable else 0))
 
     def dt_cfl(self, cfl=0.5):
         dt = ctypes.c_double()

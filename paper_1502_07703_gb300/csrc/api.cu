@@ -90,7 +90,7 @@ void free_all(pyr_dg* h) {
   for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
   h->events.clear();
   void* ptrs[] = {h->q,    h->res,  h->tr, h->geo,     h->gface, h->invM, h->tab,
-                  h->tabd, h->gtab, h->ev, h->partial, h->mapP, h->tr2, h->dt_elem};
+                  h->tabd, h->gtab, h->ev, h->partial, h->mapP, h->tr2, h->dt_elem, h->ecache};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -482,23 +482,99 @@ int pyr_dg_step(pyr_dg* h, int nsteps, double dt) {
   return PYR_DG_OK;
 }
 
+namespace {
+// Sum the error kernels' per-block pairs (synchronises the stream).
+int read_partial(pyr_dg* h, double* s0, double* s1) {
+  std::vector<double> part((size_t)h->err_blocks * 2);
+  CUDA_TRY(cudaMemcpyAsync(part.data(), h->partial, part.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < h->err_blocks; ++i) {
+    a += part[2 * i];
+    b += part[2 * i + 1];
+  }
+  *s0 = a;
+  *s1 = b;
+  return PYR_DG_OK;
+}
+
+// First pyr_dg_error of a wave handle: store the exact fields' spatial factors when the
+// store takes at most a quarter of the free device memory; otherwise the error kernel
+// evaluates them at every call.
+int build_error_cache(pyr_dg* h) {
+  h->ecache_state = -1;
+  if (h->ecache_mode == 0) return PYR_DG_OK;
+  const size_t Q = (size_t)h->N + 3;
+  const size_t bytes = (size_t)h->K * (4 * Q * Q * Q + Q * Q) * sizeof(double);
+  size_t free_b = 0, total_b = 0;
+  CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  if (bytes > free_b / 4) return PYR_DG_OK;
+  if (cudaMalloc((void**)&h->ecache, bytes) != cudaSuccess) {
+    cudaGetLastError();  // an allocation failure leaves the context usable: compute on the fly
+    h->ecache = nullptr;
+    return PYR_DG_OK;
+  }
+  double* S = h->ecache;
+  double* W = S + (size_t)h->K * 4 * Q * Q * Q;
+  h->L->exact_cache(h->K, h->ev, h->gtab, h->bc, S, W, h->partial, h->err_blocks, h->stream);
+  CUDA_TRY(cudaGetLastError());
+  const int rc = read_partial(h, &h->ecache_norm[0], &h->ecache_norm[1]);
+  if (rc != PYR_DG_OK) return rc;
+  h->ecache_state = 1;
+  return PYR_DG_OK;
+}
+}  // namespace
+
+int pyr_dg_set_error_cache(pyr_dg* h, int enable) {
+  if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
+  DeviceGuard g(h->device);
+  CUDA_TRY(g.err);
+  if (h->ecache) {
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    CUDA_TRY(cudaFree(h->ecache));
+    h->ecache = nullptr;
+  }
+  h->ecache_mode = enable ? 1 : 0;
+  h->ecache_state = 0;
+  return PYR_DG_OK;
+}
+
 int pyr_dg_error(pyr_dg* h, double* l2_abs, double* l2_rel) {
   if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
   DeviceGuard g(h->device);
   CUDA_TRY(g.err);
-  if (h->equation == PYR_DG_ADVECTION)
+  double e2 = 0.0, n2 = 0.0;
+  if (h->equation == PYR_DG_ADVECTION) {
     h->L->error1(h->K, h->q, h->ev, h->gtab, h->beta, h->box_lo, h->box_hi - h->box_lo, h->t, h->partial,
                  h->err_blocks, h->stream);
-  else
-    h->L->error(h->K, h->q, h->ev, h->gtab, h->bc, h->t, h->partial, h->err_blocks, h->stream);
-  CUDA_TRY(cudaGetLastError());
-  std::vector<double> part((size_t)h->err_blocks * 2);
-  CUDA_TRY(cudaMemcpyAsync(part.data(), h->partial, part.size() * 8, cudaMemcpyDeviceToHost, h->stream));
-  CUDA_TRY(cudaStreamSynchronize(h->stream));
-  double e2 = 0.0, n2 = 0.0;
-  for (int b = 0; b < h->err_blocks; ++b) {
-    e2 += part[2 * b];
-    n2 += part[2 * b + 1];
+    CUDA_TRY(cudaGetLastError());
+    const int rc = read_partial(h, &e2, &n2);
+    if (rc != PYR_DG_OK) return rc;
+  } else {
+    if (h->ecache_state == 0) {
+      const int rc = build_error_cache(h);
+      if (rc != PYR_DG_OK) return rc;
+    }
+    if (h->ecache_state > 0) {
+      // time factors of the standing wave: p ~ cos(sqrt3 pi sc t), u ~ sin(sqrt3 pi sc t)/sqrt3
+      const double sc = h->bc == 0 ? 1.0 : 0.5;
+      const double arg = 3.14159265358979323846 * (1.7320508075688772935 * sc * h->t);
+      const double tp = std::cos(arg), tu = std::sin(arg) * 0.57735026918962576451;
+      const size_t Q = (size_t)h->N + 3;
+      const double* S = h->ecache;
+      const double* W = S + (size_t)h->K * 4 * Q * Q * Q;
+      h->L->error_cached(h->K, h->q, h->gtab, S, W, tp, tu, h->partial, h->err_blocks, h->stream);
+      CUDA_TRY(cudaGetLastError());
+      double zero = 0.0;
+      const int rc = read_partial(h, &e2, &zero);
+      if (rc != PYR_DG_OK) return rc;
+      n2 = tp * tp * h->ecache_norm[0] + tu * tu * h->ecache_norm[1];
+    } else {
+      h->L->error(h->K, h->q, h->ev, h->gtab, h->bc, h->t, h->partial, h->err_blocks, h->stream);
+      CUDA_TRY(cudaGetLastError());
+      const int rc = read_partial(h, &e2, &n2);
+      if (rc != PYR_DG_OK) return rc;
+    }
   }
   if (l2_abs) *l2_abs = std::sqrt(e2);
   if (l2_rel) *l2_rel = n2 > 0 ? std::sqrt(e2 / n2) : std::sqrt(e2);

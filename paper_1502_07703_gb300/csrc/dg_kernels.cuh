@@ -914,4 +914,188 @@ __global__ void __launch_bounds__(ErrCfg<N>::NT)
   }
 }
 
+
+// ============================================================ cached error norm (a8)
+// The exact standing wave is S_p(x) cos(sqrt3 pi sc t) for p and S_m(x) sin(sqrt3 pi sc t)/sqrt3
+// for the velocities, with S_p = cos cos cos and S_u, S_v, S_w one sine each (of pi sc x,
+// pi sc y, pi sc z). The spatial factors at the error-rule points do not depend on t, so a
+// handle may store them once: S[(e Q^3 + x) 4 + f] at point x = p + Q q + Q^2 r, and the
+// c-independent weight W[e Q^2 + p + Q q] = w_p w_q J(a_p, b_q). Each block also sums
+// w S_p^2 and w (S_u^2 + S_v^2 + S_w^2) over its points: the exact solution's norm at any t
+// follows from those two numbers.
+template <int N>
+__global__ void __launch_bounds__(ErrCfg<N>::NT)
+    exact_cache_kernel(int64_t K, const double* __restrict__ ev, const double* __restrict__ gtab, int bc,
+                       double* __restrict__ S, double* __restrict__ W, double* __restrict__ partial) {
+  using d = Dims<N>;
+  constexpr GeoLayout G(N);
+  constexpr int Q = d::Q;
+  constexpr int NW = ErrCfg<N>::NT / 32;
+  __shared__ double v[15];
+  __shared__ double s_XB[4 * Q * Q];
+  __shared__ double red[2][NW];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const double sc = bc == 0 ? 1.0 : 0.5;
+  double sp = 0.0, su = 0.0;
+  for (int64_t e = blockIdx.x; e < K; e += gridDim.x) {
+    __syncthreads();
+    if (tid < 15) v[tid] = ev[e * 15 + tid];
+    __syncthreads();
+    for (int x = tid; x < Q * Q; x += nthr) {
+      const int p = x % Q, qq = x / Q;
+      double B[3], Ba[3], Bb[3], D[3], g1[3];
+      d_bilinear(v, gtab[G.XQ + p], gtab[G.XQ + qq], B, Ba, Bb);
+      for (int m = 0; m < 3; ++m) D[m] = 0.5 * (v[12 + m] - B[m]);
+      d_cross(Bb, D, g1);
+      const double wJ = gtab[G.WQ + p] * gtab[G.WQ + qq] * (Ba[0] * g1[0] + Ba[1] * g1[1] + Ba[2] * g1[2]);
+      s_XB[4 * x + 0] = B[0];
+      s_XB[4 * x + 1] = B[1];
+      s_XB[4 * x + 2] = B[2];
+      s_XB[4 * x + 3] = wJ;
+      W[e * Q * Q + x] = wJ;
+    }
+    __syncthreads();
+    for (int x = tid; x < Q * Q * Q; x += nthr) {
+      const int pq = x % (Q * Q), r = x / (Q * Q);
+      const double c = gtab[G.XQC + r];
+      const double* xb = s_XB + 4 * pq;
+      double sn[3], cs[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m)  // x_m = B_m (1-c)/2 + v5_m (1+c)/2 on the c line through (a, b)
+        sincospi(sc * (0.5 * (1 - c) * xb[m] + 0.5 * (1 + c) * v[12 + m]), &sn[m], &cs[m]);
+      double Sf[4];
+      Sf[0] = cs[0] * cs[1] * cs[2];
+      Sf[1] = sn[0] * cs[1] * cs[2];
+      Sf[2] = cs[0] * sn[1] * cs[2];
+      Sf[3] = cs[0] * cs[1] * sn[2];
+      double* dst = S + (e * Q * Q * Q + x) * 4;
+      reinterpret_cast<double2*>(dst)[0] = make_double2(Sf[0], Sf[1]);
+      reinterpret_cast<double2*>(dst)[1] = make_double2(Sf[2], Sf[3]);
+      const double w = xb[3] * gtab[G.WQC + r];
+      sp += w * Sf[0] * Sf[0];
+      su += w * (Sf[1] * Sf[1] + Sf[2] * Sf[2] + Sf[3] * Sf[3]);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    sp += __shfl_down_sync(0xffffffffu, sp, off);
+    su += __shfl_down_sync(0xffffffffu, su, off);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = sp;
+    red[1][tid >> 5] = su;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < NW; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    partial[2 * blockIdx.x] = a;
+    partial[2 * blockIdx.x + 1] = b;
+  }
+}
+
+template <int N>
+struct ErrCSmem {
+  using d = Dims<N>;
+  static constexpr int Q = d::Q;
+  static constexpr size_t u = 0;
+  static constexpr size_t A = u + 4 * d::Np;
+  static constexpr size_t B = A + 4 * d::nrow * Q;
+  static constexpr size_t LQ = B + 4 * d::n1 * Q * Q;
+  static constexpr size_t GQ = LQ + d::nrow * Q;
+  static constexpr size_t W = GQ + d::n1 * Q;
+  static constexpr size_t total = W + Q * Q;
+  static constexpr size_t bytes = total * sizeof(double);
+};
+
+// The error norm's sum of w (U_h - U_exact)^2 with the exact fields from the cache:
+// U_exact = S_f tp (f = 0) or S_f tu (velocities), tp = cos(sqrt3 pi sc t), tu = sin(...)/sqrt3.
+// U_h at the points by the same a, b, c passes as error_kernel. partial[2 b] gets the block's
+// sum, partial[2 b + 1] zero.
+template <int N, typename T>
+__global__ void __launch_bounds__(ErrCfg<N>::NT)
+    error_cached_kernel(int64_t K, const T* __restrict__ q, const double* __restrict__ gtab,
+                        const double* __restrict__ S, const double* __restrict__ W, double tp, double tu,
+                        double* __restrict__ partial) {
+  using d = Dims<N>;
+  using SM = ErrCSmem<N>;
+  constexpr GeoLayout G(N);
+  constexpr int Q = d::Q;
+  constexpr int NW = ErrCfg<N>::NT / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sm = reinterpret_cast<double*>(smem_raw);
+  double* s_u = sm + SM::u;
+  double* s_A = sm + SM::A;
+  double* s_B = sm + SM::B;
+  double* s_LQ = sm + SM::LQ;
+  double* s_GQ = sm + SM::GQ;
+  double* s_W = sm + SM::W;
+  __shared__ double red[NW];
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int x = tid; x < d::nrow * Q; x += nthr) s_LQ[x] = gtab[G.LQ + x];
+  for (int x = tid; x < d::n1 * Q; x += nthr) s_GQ[x] = gtab[G.GQ + x];
+  double e2 = 0.0;
+  for (int64_t e = blockIdx.x; e < K; e += gridDim.x) {
+    __syncthreads();
+    for (int x = tid; x < 4 * d::Np; x += nthr) s_u[x] = (double)q[e * 4 * d::Np + x];
+    for (int x = tid; x < Q * Q; x += nthr) s_W[x] = W[e * Q * Q + x];
+    __syncthreads();
+    for (int x = tid; x < 4 * d::nrow * Q; x += nthr) {  // a pass, level-major
+      int k = 0;
+      while (x >= 4 * Q * tri_num(k + 1)) ++k;
+      const int rem = x - 4 * Q * tri_num(k);
+      const int f = rem / ((k + 1) * Q);
+      const int j = (rem / Q) % (k + 1);
+      const int p = rem % Q;
+      const double* uc = s_u + f * d::Np + lvl_off(k) + j * (k + 1);
+      const double* lq = s_LQ + tri_num(k) * Q + p;
+      double acc = 0;
+      for (int i = 0; i <= k; ++i) acc += uc[i] * lq[i * Q];
+      s_A[(f * d::nrow + tri_num(k) + j) * Q + p] = acc;
+    }
+    __syncthreads();
+    for (int x = tid; x < 4 * d::n1 * Q * Q; x += nthr) {  // b pass, level-major
+      const int pq = x % (Q * Q);
+      const int tt = x / (Q * Q);
+      const int f = tt % 4, k = tt / 4;
+      const int p = pq % Q, qq = pq / Q;
+      const double* Ar = s_A + (f * d::nrow + tri_num(k)) * Q + p;
+      const double* lq = s_LQ + tri_num(k) * Q + qq;
+      double acc = 0;
+      for (int j = 0; j <= k; ++j) acc += Ar[j * Q] * lq[j * Q];
+      s_B[(f * d::n1 + k) * Q * Q + pq] = acc;
+    }
+    __syncthreads();
+    for (int x = tid; x < Q * Q * Q; x += nthr) {  // c pass and the error integrand
+      const int pq = x % (Q * Q), r = x / (Q * Q);
+      const double2* sx = reinterpret_cast<const double2*>(S + (e * Q * Q * Q + x) * 4);
+      const double2 s01 = sx[0], s23 = sx[1];
+      const double Sf[4] = {s01.x * tp, s01.y * tu, s23.x * tu, s23.y * tu};
+      double ept = 0.0;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        double uh = 0;
+#pragma unroll
+        for (int k = 0; k <= N; ++k) uh += s_GQ[k * Q + r] * s_B[(f * d::n1 + k) * Q * Q + pq];
+        const double df = uh - Sf[f];
+        ept += df * df;
+      }
+      e2 += s_W[pq] * gtab[G.WQC + r] * ept;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, off);
+  if ((tid & 31) == 0) red[tid >> 5] = e2;
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0;
+    for (int w = 0; w < NW; ++w) a += red[w];
+    partial[2 * blockIdx.x] = a;
+    partial[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
 }  // namespace pyrdg

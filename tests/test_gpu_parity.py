@@ -318,9 +318,40 @@ def test_error_norm_fine_meshes(torch_cuda, nx, bc):
     U = random_state(dg.K, dg.Np, 21)
     with _solver(v, e, N, bc=bc) as s:
         s.set_state(U, t=0.3)
-        err_gpu = s.error()
+        err_gpu = s.error()  # first call stores the exact fields' spatial factors
+        err_again = s.error()
+        s.set_error_cache(False)
+        err_direct = s.error()  # exact fields evaluated in the kernel
     err_or = dg.error(dg.psi_from_phi(U), 0.3)
-    np.testing.assert_allclose(err_gpu, err_or, rtol=1e-12)
+    for err in (err_gpu, err_again, err_direct):
+        np.testing.assert_allclose(err, err_or, rtol=1e-12)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_error_norm_store_matches_direct(torch_cuda, precision):
+    """The stored spatial factors give the same error norm as the direct kernel at several
+    times (the time factors come from the host), and the store takes the device memory the
+    header states and gives it back when switched off."""
+    import torch
+    v, e = make_pyramid_mesh(6, delta=0.05, seed=7)
+    N = 3
+    with _solver(v, e, N, precision=precision) as s:
+        U = random_state(s.K, s.Np, 31).astype(s.np_dtype)
+        Q = N + 3
+        store = s.K * (4 * Q ** 3 + Q ** 2) * 8
+        for t in (0.0, 0.37, 1.9):
+            s.set_state(U, t=t)
+            s.set_error_cache(False)
+            direct = s.error()
+            free0 = torch.cuda.mem_get_info()[0]
+            s.set_error_cache(True)
+            stored = s.error()
+            free1 = torch.cuda.mem_get_info()[0]
+            assert free0 - free1 >= store, (free0, free1, store)
+            np.testing.assert_allclose(s.error(), direct, rtol=1e-12)
+            np.testing.assert_allclose(stored, direct, rtol=1e-12)
+        s.set_error_cache(False)
+        assert torch.cuda.mem_get_info()[0] - free1 >= store
 
 
 @pytest.mark.parametrize("nx,N", [(32, 5), (16, 7)])
