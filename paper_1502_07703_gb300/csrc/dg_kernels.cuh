@@ -286,26 +286,30 @@ __device__ __forceinline__ void trace_passes(const T* s_tab, const T* s_u, T* s_
   }
   __syncthreads();
   // c pass: sum over levels with G_k(-1) (base) or G_k(c_m) (triangles)
+  // One code path for both kinds of face (only the weight row and the column differ), so
+  // that a warp holding base and triangle points runs the sums once.
   for (int g = tid; g < d::Nfc; g += nthr) {
     const int face = g / d::n2, idx = g % d::n2;
-    T out[4];
+    const T* cw;  // weights of levels k = 0..N at stride cs
+    int cs, col;  // s_B column
     if (face == 0) {
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        T acc = 0;
-        for (int k = 0; k <= N; ++k) acc += s_tab[L.GB + k] * s_B[(f * d::n1 + k) * S::nB + idx];
-        out[f] = acc;
-      }
+      cw = s_tab + L.GB;
+      cs = 1;
+      col = idx;
     } else {
       const int ee = idx % d::n1, m = idx / d::n1;
       const int slot = face == 1 ? 0 : face == 3 ? 1 : face == 4 ? 2 : 3;
-      const int s = d::n2 + slot * d::n1 + ee;
+      cw = s_tab + L.GF + m;
+      cs = d::n1;
+      col = d::n2 + slot * d::n1 + ee;
+    }
+    T out[4];
 #pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        T acc = 0;
-        for (int k = 0; k <= N; ++k) acc += s_tab[L.GF + k * d::n1 + m] * s_B[(f * d::n1 + k) * S::nB + s];
-        out[f] = acc;
-      }
+    for (int f = 0; f < 4; ++f) {
+      T acc = 0;
+#pragma unroll
+      for (int k = 0; k <= N; ++k) acc += cw[k * cs] * s_B[(f * d::n1 + k) * S::nB + col];
+      out[f] = acc;
     }
     T* dst = tr_e + g * 4;
 #pragma unroll
