@@ -505,11 +505,24 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
 #pragma unroll
     for (int f = 0; f < 4; ++f) s_Fs[f * d::Nfc + g] = F[f];
   }
-  // a pass, level-major: A = l^k(a_p) u, dA = l^k'(a_p) u
+  // a pass, level-major: A = l^k(a_p) u, dA = l^k'(a_p) u. Levels run in the order
+  // 1..N-1, 0, N: the warp that straddles into level N's short form then also holds
+  // the cheapest level.
+  constexpr int aLow = 4 * d::n1 * (tri_num(N) - 1);  // items of levels 1..N-1
   for (int x = tid; x < 4 * d::nrow * d::n1; x += nthr) {
-    int k = 0;
-    while (x >= 4 * d::n1 * tri_num(k + 1)) ++k;
-    const int rem = x - 4 * d::n1 * tri_num(k);
+    int k, rem;
+    if (x < aLow) {
+      const int y = x + 4 * d::n1;
+      k = 1;
+      while (y >= 4 * d::n1 * tri_num(k + 1)) ++k;
+      rem = y - 4 * d::n1 * tri_num(k);
+    } else if (x < aLow + 4 * d::n1) {
+      k = 0;
+      rem = x - aLow;
+    } else {
+      k = N;
+      rem = x - 4 * d::n1 * tri_num(N);
+    }
     const int f = rem / ((k + 1) * d::n1);
     const int j = (rem / d::n1) % (k + 1);
     const int p = rem % d::n1;
