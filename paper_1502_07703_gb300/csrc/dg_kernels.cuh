@@ -329,7 +329,10 @@ __global__ void __launch_bounds__(KCfg<N>::NT) trace_kernel(int64_t K, const T* 
   T* s_u = sm + S::u;
   const int64_t e = blockIdx.x;
   const int tid = threadIdx.x;
-  for (int x = tid; x < L.size; x += blockDim.x) s_tab[x] = tab[x];
+  // the passes read LX, GB and GF only (GF follows GB in the table)
+  static_assert(L.LX == 0 && L.GF == L.GB + d::n1, "trace table ranges");
+  for (int x = tid; x < d::nrow * d::P3; x += blockDim.x) s_tab[x] = tab[x];
+  for (int x = L.GB + tid; x < L.GF + d::n2; x += blockDim.x) s_tab[x] = tab[x];
   for (int x = tid; x < 4 * d::Np; x += blockDim.x) s_u[x] = q[e * 4 * d::Np + x];
   __syncthreads();
   trace_passes<N, T>(s_tab, s_u, sm + S::A, sm + S::B, tr + e * d::Nfc * 4, tid, blockDim.x);
@@ -1090,14 +1093,14 @@ __global__ void __launch_bounds__(ErrCfg<N>::NT)
       const int pq = x % (Q * Q), r = x / (Q * Q);
       const double2* sx = reinterpret_cast<const double2*>(S + (e * Q * Q * Q + x) * 4);
       const double2 s01 = sx[0], s23 = sx[1];
-      const double Sf[4] = {s01.x * tp, s01.y * tu, s23.x * tu, s23.y * tu};
+      const double Sf[4] = {s01.x, s01.y, s23.x, s23.y};
       double ept = 0.0;
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
         double uh = 0;
 #pragma unroll
         for (int k = 0; k <= N; ++k) uh += s_GQ[k * Q + r] * s_B[(f * d::n1 + k) * Q * Q + pq];
-        const double df = uh - Sf[f];
+        const double df = fma(-Sf[f], f == 0 ? tp : tu, uh);  // U_h - U_exact
         ept += df * df;
       }
       e2 += s_W[pq] * gtab[G.WQC + r] * ept;
