@@ -168,15 +168,16 @@ int pyr_dg_step(pyr_dg* h, int nsteps, double dt);
 int pyr_dg_error(pyr_dg* h, double* l2_abs, double* l2_rel);
 /* The exact fields are products of cos/sin(pi sc x), sc = 1 (wall) or 1/2 (free
  * surface), times cos or sin of sqrt3 pi sc t; only the time factors change between
- * calls. On a wave handle the first pyr_dg_error stores the spatial factors at the
+ * calls. On a wave handle the second pyr_dg_error stores the spatial factors at the
  * error-rule points, with the c-independent weights: K (4 (N+3)^3 + (N+3)^2) doubles
  * of device memory, allocated only when that is at most a quarter of the free device
- * memory, and freed by pyr_dg_destroy. Later calls then evaluate only U_h at the
- * points. Without the store every call evaluates the exact fields itself. Both give
- * the same integral up to rounding. */
+ * memory, and freed by pyr_dg_destroy. That call and later ones then evaluate only U_h
+ * at the points. Without the store (the first call, or when it does not fit) the call
+ * evaluates the exact fields itself. Both give the same integral up to rounding. */
 
 /* enable = 0: free the stored factors and evaluate the exact fields at every call;
- * enable != 0 (the default): store them at the next pyr_dg_error when they fit.
+ * enable != 0 (the default): store them at the second pyr_dg_error from now when
+ * they fit.
  * Synchronises the handle's stream when it frees the store. */
 int pyr_dg_set_error_cache(pyr_dg* h, int enable);
 

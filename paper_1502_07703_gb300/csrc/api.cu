@@ -498,9 +498,9 @@ int read_partial(pyr_dg* h, double* s0, double* s1) {
   return PYR_DG_OK;
 }
 
-// First pyr_dg_error of a wave handle: store the exact fields' spatial factors when the
-// store takes at most a quarter of the free device memory; otherwise the error kernel
-// evaluates them at every call.
+// Second pyr_dg_error of a wave handle (a single call does not pay for the store): store
+// the exact fields' spatial factors when the store takes at most a quarter of the free
+// device memory; otherwise the error kernel evaluates them at every call.
 int build_error_cache(pyr_dg* h) {
   h->ecache_state = -1;
   if (h->ecache_mode == 0) return PYR_DG_OK;
@@ -551,9 +551,11 @@ int pyr_dg_error(pyr_dg* h, double* l2_abs, double* l2_rel) {
     const int rc = read_partial(h, &e2, &n2);
     if (rc != PYR_DG_OK) return rc;
   } else {
-    if (h->ecache_state == 0) {
+    if (h->ecache_state == 2) {
       const int rc = build_error_cache(h);
       if (rc != PYR_DG_OK) return rc;
+    } else if (h->ecache_state == 0) {
+      h->ecache_state = 2;
     }
     if (h->ecache_state > 0) {
       // time factors of the standing wave: p ~ cos(sqrt3 pi sc t), u ~ sin(sqrt3 pi sc t)/sqrt3

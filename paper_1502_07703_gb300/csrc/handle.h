@@ -44,8 +44,8 @@ struct pyr_dg {
   void* dt_elem = nullptr;
   // pyr_dg_error's store of the exact fields' spatial factors at the error-rule points
   // (K (4 Q^3 + Q^2) doubles, Q = N+3) and their two weighted sums of squares.
-  // ecache_mode: 1 store when it fits (default), 0 never. ecache_state: 0 not tried,
-  // 1 stored, -1 not stored (too large, or mode 0).
+  // ecache_mode: 1 store when it fits (default), 0 never. ecache_state: 0 no call yet,
+  // 2 one call made without the store, 1 stored, -1 not stored (too large, or mode 0).
   double* ecache = nullptr;
   double ecache_norm[2] = {0.0, 0.0};
   int ecache_mode = 1, ecache_state = 0;

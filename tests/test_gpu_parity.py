@@ -318,12 +318,11 @@ def test_error_norm_fine_meshes(torch_cuda, nx, bc):
     U = random_state(dg.K, dg.Np, 21)
     with _solver(v, e, N, bc=bc) as s:
         s.set_state(U, t=0.3)
-        err_gpu = s.error()  # first call stores the exact fields' spatial factors
+        err_gpu = s.error()  # exact fields evaluated in the kernel
+        err_stored = s.error()  # the second call stores their spatial factors
         err_again = s.error()
-        s.set_error_cache(False)
-        err_direct = s.error()  # exact fields evaluated in the kernel
     err_or = dg.error(dg.psi_from_phi(U), 0.3)
-    for err in (err_gpu, err_again, err_direct):
+    for err in (err_gpu, err_stored, err_again):
         np.testing.assert_allclose(err, err_or, rtol=1e-12)
 
 
@@ -345,6 +344,8 @@ def test_error_norm_store_matches_direct(torch_cuda, precision):
             direct = s.error()
             free0 = torch.cuda.mem_get_info()[0]
             s.set_error_cache(True)
+            np.testing.assert_allclose(s.error(), direct, rtol=1e-12)  # no store at one call
+            assert free0 - torch.cuda.mem_get_info()[0] < store
             stored = s.error()
             free1 = torch.cuda.mem_get_info()[0]
             assert free0 - free1 >= store, (free0, free1, store)
