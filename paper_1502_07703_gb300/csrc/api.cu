@@ -557,7 +557,7 @@ int pyr_dg_error(pyr_dg* h, double* l2_abs, double* l2_rel) {
     } else if (h->ecache_state == 0) {
       h->ecache_state = 2;
     }
-    if (h->ecache_state > 0) {
+    if (h->ecache_state == 1 && h->ecache) {
       // time factors of the standing wave: p ~ cos(sqrt3 pi sc t), u ~ sin(sqrt3 pi sc t)/sqrt3
       const double sc = h->bc == 0 ? 1.0 : 0.5;
       const double arg = 3.14159265358979323846 * (1.7320508075688772935 * sc * h->t);
