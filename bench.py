@@ -496,10 +496,10 @@ def main():
     flops_el = rhs_flops_per_element(nd) + (trace_flops_per_element(nd) if prec == "f32" else 0)
     achieved = flops_el * K / rhs_avg_s / 1e12
     # DRAM bytes per element of the FP64 fused stage kernel, from the ncu capture summarised
-    # in profiles/rhs_kernel_n4_f64_24cube.md (82,944 pyramids, N = 4: 1195.8 MB read +
+    # in profiles/rhs_kernel_n4_f64_24cube.md (82,944 pyramids, N = 4: 1195.2 MB read +
     # write per launch), scaled by the element count. Valid for that kernel version only:
     # set to None when the kernel changes, until it is measured again.
-    traffic = 14416.0 * K if (nd == 4 and prec == "f64" and args.nx >= 24) else None
+    traffic = 14410.0 * K if (nd == 4 and prec == "f64" and args.nx >= 24) else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": f"rhs_kernel<{nd},double,update>" if prec == "f64" else f"stage32_kernel<{nd}>",
                 "peak_kind": f"{prec.upper()} FMA throughput measured in this run",
