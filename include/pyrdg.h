@@ -166,14 +166,18 @@ int pyr_dg_step(pyr_dg* h, int nsteps, double dt);
  * Gauss-Jacobi (2,0) in c), over all four fields; l2_rel divides by the L2
  * norm of the exact solution. Either pointer may be NULL. Synchronises. */
 int pyr_dg_error(pyr_dg* h, double* l2_abs, double* l2_rel);
-/* The exact fields are products of cos/sin(pi sc x), sc = 1 (wall) or 1/2 (free
- * surface), times cos or sin of sqrt3 pi sc t; only the time factors change between
- * calls. On a wave handle the second pyr_dg_error stores the spatial factors at the
- * error-rule points, with the c-independent weights: K (4 (N+3)^3 + (N+3)^2) doubles
- * of device memory, allocated only when that is at most a quarter of the free device
- * memory, and freed by pyr_dg_destroy. That call and later ones then evaluate only U_h
- * at the points. Without the store (the first call, or when it does not fit) the call
- * evaluates the exact fields itself. Both give the same integral up to rounding. */
+/* The exact fields are S(x) times a time factor: S = products of cos/sin(pi sc x),
+ * sc = 1 (wall) or 1/2 (free surface), times cos or sin of sqrt3 pi sc t. Let P be the
+ * projection onto each element's polynomial space under the error rule's inner product;
+ * that rule integrates the mass matrix exactly, so M is the diagonal of Lemma 3. Then,
+ * per field, the squared error is sum_i M_ii (u_i - T s_i)^2 + T^2 |P S - S|^2 with s the
+ * coefficients of P S, and only the time factor T changes between calls. On a wave
+ * handle the second pyr_dg_error stores s, M in double and the mesh sums of |P S - S|^2
+ * and |S|^2: 5 K Np doubles of device memory (plus 4 per error block), allocated only
+ * when that is at most a quarter of the free device memory, and freed by
+ * pyr_dg_destroy. That call and later ones then read only the coefficients. Without
+ * the store (the first call, or when it does not fit) the call evaluates U_h and the
+ * exact fields at the error-rule points. Both give the same value up to rounding. */
 
 /* enable = 0: free the stored factors and evaluate the exact fields at every call;
  * enable != 0 (the default): store them at the second pyr_dg_error from now when

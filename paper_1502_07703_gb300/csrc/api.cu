@@ -498,14 +498,16 @@ int read_partial(pyr_dg* h, double* s0, double* s1) {
   return PYR_DG_OK;
 }
 
-// Second pyr_dg_error of a wave handle (a single call does not pay for the store): store
-// the exact fields' spatial factors when the store takes at most a quarter of the free
-// device memory; otherwise the error kernel evaluates them at every call.
+// Second pyr_dg_error of a wave handle (a single call does not pay for the store): store the
+// error rule's projection of the exact fields' spatial factors, the mass diagonal and four
+// mesh sums, when that takes at most a quarter of the free device memory; otherwise the
+// error kernel evaluates the exact fields at its points at every call.
 int build_error_cache(pyr_dg* h) {
   h->ecache_state = -1;
   if (h->ecache_mode == 0) return PYR_DG_OK;
-  const size_t Q = (size_t)h->N + 3;
-  const size_t bytes = (size_t)h->K * (4 * Q * Q * Q + Q * Q) * sizeof(double);
+  const size_t Np = (size_t)h->Np;
+  const size_t nproj = (size_t)h->K * 5 * Np, npart = (size_t)h->err_blocks * 4;
+  const size_t bytes = (nproj + npart) * sizeof(double);
   size_t free_b = 0, total_b = 0;
   CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   if (bytes > free_b / 4) return PYR_DG_OK;
@@ -514,12 +516,19 @@ int build_error_cache(pyr_dg* h) {
     h->ecache = nullptr;
     return PYR_DG_OK;
   }
-  double* S = h->ecache;
-  double* W = S + (size_t)h->K * 4 * Q * Q * Q;
-  h->L->exact_cache(h->K, h->ev, h->gtab, h->bc, S, W, h->partial, h->err_blocks, h->stream);
+  double* shat = h->ecache;
+  double* Md = shat + (size_t)h->K * 4 * Np;
+  double* part = h->ecache + nproj;
+  h->L->exact_proj(h->K, h->ev, h->gtab, h->bc, shat, Md, part, h->err_blocks, h->stream);
   CUDA_TRY(cudaGetLastError());
-  const int rc = read_partial(h, &h->ecache_norm[0], &h->ecache_norm[1]);
-  if (rc != PYR_DG_OK) return rc;
+  std::vector<double> hp(npart);
+  CUDA_TRY(cudaMemcpyAsync(hp.data(), part, npart * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  for (int c = 0; c < 4; ++c) {
+    double a = 0.0;
+    for (int b = 0; b < h->err_blocks; ++b) a += hp[4 * (size_t)b + c];
+    h->ecache_sum[c] = a;
+  }
   h->ecache_state = 1;
   return PYR_DG_OK;
 }
@@ -562,15 +571,16 @@ int pyr_dg_error(pyr_dg* h, double* l2_abs, double* l2_rel) {
       const double sc = h->bc == 0 ? 1.0 : 0.5;
       const double arg = 3.14159265358979323846 * (1.7320508075688772935 * sc * h->t);
       const double tp = std::cos(arg), tu = std::sin(arg) * 0.57735026918962576451;
-      const size_t Q = (size_t)h->N + 3;
-      const double* S = h->ecache;
-      const double* W = S + (size_t)h->K * 4 * Q * Q * Q;
-      h->L->error_cached(h->K, h->q, h->gtab, S, W, tp, tu, h->partial, h->err_blocks, h->stream);
+      const double* shat = h->ecache;
+      const double* Md = shat + (size_t)h->K * 4 * h->Np;
+      h->L->error_proj(h->K, h->q, shat, Md, tp, tu, h->partial, h->err_blocks, h->stream);
       CUDA_TRY(cudaGetLastError());
       double zero = 0.0;
       const int rc = read_partial(h, &e2, &zero);
       if (rc != PYR_DG_OK) return rc;
-      n2 = tp * tp * h->ecache_norm[0] + tu * tu * h->ecache_norm[1];
+      // |U_h - U_ex|^2 = sum M (u - T s)^2 + T^2 |PS - S|^2, per field (orthogonality of P)
+      e2 += tp * tp * h->ecache_sum[0] + tu * tu * h->ecache_sum[1];
+      n2 = tp * tp * h->ecache_sum[2] + tu * tu * h->ecache_sum[3];
     } else {
       h->L->error(h->K, h->q, h->ev, h->gtab, h->bc, h->t, h->partial, h->err_blocks, h->stream);
       CUDA_TRY(cudaGetLastError());

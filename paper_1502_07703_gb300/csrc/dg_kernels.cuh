@@ -935,184 +935,203 @@ __global__ void __launch_bounds__(ErrCfg<N>::NT)
 }
 
 
-// ============================================================ cached error norm (a8)
-// The exact standing wave is S_p(x) cos(sqrt3 pi sc t) for p and S_m(x) sin(sqrt3 pi sc t)/sqrt3
-// for the velocities, with S_p = cos cos cos and S_u, S_v, S_w one sine each (of pi sc x,
-// pi sc y, pi sc z). The spatial factors at the error-rule points do not depend on t, so a
-// handle may store them once: S[(e Q^3 + x) 4 + f] at point x = p + Q q + Q^2 r, and the
-// c-independent weight W[e Q^2 + p + Q q] = w_p w_q J(a_p, b_q). Each block also sums
-// w S_p^2 and w (S_u^2 + S_v^2 + S_w^2) over its points: the exact solution's norm at any t
-// follows from those two numbers.
+// ============================================================ error norm from coefficients (a8)
+// The exact standing wave is S_p(x) tp(t) for p and S_m(x) tu(t) for the velocities, with
+// S_p = cos cos cos and S_u, S_v, S_w one sine each (of pi sc x, pi sc y, pi sc z), and
+// tp = cos(sqrt3 pi sc t), tu = sin(sqrt3 pi sc t)/sqrt3. Write <.,.>_Q for the error rule's
+// inner product ((N+3)-point rules) and P for the <.,.>_Q-orthogonal projection onto one
+// element's polynomial space. The rule integrates the mass matrix exactly, so under it M is
+// the diagonal of Lemma 3. With U_h in that space, U_h - P U_ex is orthogonal to
+// P U_ex - U_ex, hence per field
+//   |U_h - U_ex|_Q^2 = sum_i M_ii (u_i - T s_i)^2 + T^2 |P S - S|_Q^2,
+// s = coefficients of P S, T = tp or tu. The second term and |S|_Q^2 do not depend on t.
+// exact_proj_kernel computes, once per handle: s (shat[e][f][n]), M_ii (Mdiag[e][n]) and,
+// per block, the sums of |P S_p - S_p|^2, |P S_m - S_m|^2 over m, |S_p|^2 and |S_m|^2 over m
+// (partial[4 b + 0..3]). error_proj_kernel then sums M_ii (u_i - T s_i)^2 at any t.
+template <int N>
+struct ProjQSmem {
+  using d = Dims<N>;
+  static constexpr int Q = d::Q;
+  static constexpr size_t u = 0;                      // 4 Np: coefficients s
+  static constexpr size_t F = u + 4 * d::Np;          // 4 Q^3: w S at the points
+  static constexpr size_t S = F + 4 * Q * Q * Q;      // 4 Q^3: S at the points
+  static constexpr size_t C = S + 4 * Q * Q * Q;      // 4 n1 Q^2: c^T sums, then the forward b pass
+  static constexpr size_t Bt = C + 4 * d::n1 * Q * Q; // 4 nrow Q: b^T sums, then the forward a pass
+  static constexpr size_t XB = Bt + 4 * d::nrow * Q;  // 4 Q^2: B(a,b) and w_p w_q J(a,b)
+  static constexpr size_t LQ = XB + 4 * Q * Q;
+  static constexpr size_t GQ = LQ + d::nrow * Q;
+  static constexpr size_t total = GQ + d::n1 * Q;
+  static constexpr size_t bytes = total * sizeof(double);
+};
+
 template <int N>
 __global__ void __launch_bounds__(ErrCfg<N>::NT)
-    exact_cache_kernel(int64_t K, const double* __restrict__ ev, const double* __restrict__ gtab, int bc,
-                       double* __restrict__ S, double* __restrict__ W, double* __restrict__ partial) {
+    exact_proj_kernel(int64_t K, const double* __restrict__ ev, const double* __restrict__ gtab, int bc,
+                      double* __restrict__ shat, double* __restrict__ Mdiag, double* __restrict__ partial) {
   using d = Dims<N>;
+  using SM = ProjQSmem<N>;
   constexpr GeoLayout G(N);
-  constexpr int Q = d::Q;
+  constexpr int Q = d::Q, Q2 = Q * Q, Q3 = Q * Q * Q;
   constexpr int NW = ErrCfg<N>::NT / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sm = reinterpret_cast<double*>(smem_raw);
+  double* s_u = sm + SM::u;
+  double* s_F = sm + SM::F;
+  double* s_S = sm + SM::S;
+  double* s_C = sm + SM::C;
+  double* s_Bt = sm + SM::Bt;
+  double* s_XB = sm + SM::XB;
+  double* s_LQ = sm + SM::LQ;
+  double* s_GQ = sm + SM::GQ;
   __shared__ double v[15];
-  __shared__ double s_XB[4 * Q * Q];
-  __shared__ double red[2][NW];
+  __shared__ double red[4][NW];
   const int tid = threadIdx.x, nthr = blockDim.x;
+  for (int x = tid; x < d::nrow * Q; x += nthr) s_LQ[x] = gtab[G.LQ + x];
+  for (int x = tid; x < d::n1 * Q; x += nthr) s_GQ[x] = gtab[G.GQ + x];
   const double sc = bc == 0 ? 1.0 : 0.5;
-  double sp = 0.0, su = 0.0;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // |PS_p - S_p|^2, sum_m |PS_m - S_m|^2, |S_p|^2, sum_m |S_m|^2
   for (int64_t e = blockIdx.x; e < K; e += gridDim.x) {
     __syncthreads();
     if (tid < 15) v[tid] = ev[e * 15 + tid];
     __syncthreads();
-    for (int x = tid; x < Q * Q; x += nthr) {
+    for (int x = tid; x < Q2; x += nthr) {
       const int p = x % Q, qq = x / Q;
       double B[3], Ba[3], Bb[3], D[3], g1[3];
       d_bilinear(v, gtab[G.XQ + p], gtab[G.XQ + qq], B, Ba, Bb);
       for (int m = 0; m < 3; ++m) D[m] = 0.5 * (v[12 + m] - B[m]);
       d_cross(Bb, D, g1);
-      const double wJ = gtab[G.WQ + p] * gtab[G.WQ + qq] * (Ba[0] * g1[0] + Ba[1] * g1[1] + Ba[2] * g1[2]);
       s_XB[4 * x + 0] = B[0];
       s_XB[4 * x + 1] = B[1];
       s_XB[4 * x + 2] = B[2];
-      s_XB[4 * x + 3] = wJ;
-      W[e * Q * Q + x] = wJ;
+      s_XB[4 * x + 3] = gtab[G.WQ + p] * gtab[G.WQ + qq] * (Ba[0] * g1[0] + Ba[1] * g1[1] + Ba[2] * g1[2]);
     }
     __syncthreads();
-    for (int x = tid; x < Q * Q * Q; x += nthr) {
-      const int pq = x % (Q * Q), r = x / (Q * Q);
+    for (int x = tid; x < Q3; x += nthr) {  // S and w S at every point
+      const int pq = x % Q2, r = x / Q2;
       const double c = gtab[G.XQC + r];
       const double* xb = s_XB + 4 * pq;
       double sn[3], cs[3];
 #pragma unroll
       for (int m = 0; m < 3; ++m)  // x_m = B_m (1-c)/2 + v5_m (1+c)/2 on the c line through (a, b)
         sincospi(sc * (0.5 * (1 - c) * xb[m] + 0.5 * (1 + c) * v[12 + m]), &sn[m], &cs[m]);
-      double Sf[4];
-      Sf[0] = cs[0] * cs[1] * cs[2];
-      Sf[1] = sn[0] * cs[1] * cs[2];
-      Sf[2] = cs[0] * sn[1] * cs[2];
-      Sf[3] = cs[0] * cs[1] * sn[2];
-      double* dst = S + (e * Q * Q * Q + x) * 4;
-      reinterpret_cast<double2*>(dst)[0] = make_double2(Sf[0], Sf[1]);
-      reinterpret_cast<double2*>(dst)[1] = make_double2(Sf[2], Sf[3]);
+      const double Sf[4] = {cs[0] * cs[1] * cs[2], sn[0] * cs[1] * cs[2], cs[0] * sn[1] * cs[2],
+                            cs[0] * cs[1] * sn[2]};
       const double w = xb[3] * gtab[G.WQC + r];
-      sp += w * Sf[0] * Sf[0];
-      su += w * (Sf[1] * Sf[1] + Sf[2] * Sf[2] + Sf[3] * Sf[3]);
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        s_S[f * Q3 + x] = Sf[f];
+        s_F[f * Q3 + x] = w * Sf[f];
+      }
+      acc[2] += w * Sf[0] * Sf[0];
+      acc[3] += w * (Sf[1] * Sf[1] + Sf[2] * Sf[2] + Sf[3] * Sf[3]);
+    }
+    __syncthreads();
+    // <phi_n, S>_Q by transposed passes: c^T, then b^T, then a^T
+    for (int x = tid; x < 4 * d::n1 * Q2; x += nthr) {
+      const int pq = x % Q2, t = x / Q2;
+      const int k = t % d::n1, f = t / d::n1;
+      double a = 0;
+      for (int r = 0; r < Q; ++r) a += s_GQ[k * Q + r] * s_F[f * Q3 + r * Q2 + pq];
+      s_C[(f * d::n1 + k) * Q2 + pq] = a;
+    }
+    __syncthreads();
+    for (int x = tid; x < 4 * d::nrow * Q; x += nthr) {
+      const int p = x % Q, t = x / Q;
+      const int row = t % d::nrow, f = t / d::nrow;
+      int k, j;
+      decode_row(row, k, j);
+      double a = 0;
+      for (int q2 = 0; q2 < Q; ++q2)
+        a += s_LQ[(tri_num(k) + j) * Q + q2] * s_C[(f * d::n1 + k) * Q2 + p + Q * q2];
+      s_Bt[(f * d::nrow + row) * Q + p] = a;
+    }
+    __syncthreads();
+    for (int x = tid; x < 4 * d::Np; x += nthr) {  // s = M^{-1} <phi, S>_Q, M_ii = J w_i w_j C_k
+      const int f = x / d::Np, n = x % d::Np;
+      int k, j, i;
+      decode_mode(n, k, j, i);
+      double a = 0;
+      for (int p = 0; p < Q; ++p) a += s_LQ[(tri_num(k) + i) * Q + p] * s_Bt[(f * d::nrow + tri_num(k) + j) * Q + p];
+      const double J = d_jacobian(v, gtab[G.XL + tri_num(k) + i], gtab[G.XL + tri_num(k) + j]);
+      const double M = J / gtab[G.IMR + n];
+      const double sv = a / M;
+      s_u[x] = sv;
+      shat[e * 4 * d::Np + x] = sv;
+      if (f == 0) Mdiag[e * d::Np + n] = M;
+    }
+    __syncthreads();
+    // P S at the points (a, b, c passes), and |P S - S|_Q^2
+    for (int x = tid; x < 4 * d::nrow * Q; x += nthr) {
+      const int p = x % Q, t = x / Q;
+      const int row = t % d::nrow, f = t / d::nrow;
+      int k, j;
+      decode_row(row, k, j);
+      const double* uc = s_u + f * d::Np + lvl_off(k) + j * (k + 1);
+      double a = 0;
+      for (int i = 0; i <= k; ++i) a += uc[i] * s_LQ[(tri_num(k) + i) * Q + p];
+      s_Bt[(f * d::nrow + row) * Q + p] = a;
+    }
+    __syncthreads();
+    for (int x = tid; x < 4 * d::n1 * Q2; x += nthr) {
+      const int pq = x % Q2, t = x / Q2;
+      const int k = t % d::n1, f = t / d::n1;
+      const int p = pq % Q, qq = pq / Q;
+      double a = 0;
+      for (int j = 0; j <= k; ++j) a += s_Bt[(f * d::nrow + tri_num(k) + j) * Q + p] * s_LQ[(tri_num(k) + j) * Q + qq];
+      s_C[(f * d::n1 + k) * Q2 + pq] = a;
+    }
+    __syncthreads();
+    for (int x = tid; x < Q3; x += nthr) {
+      const int pq = x % Q2, r = x / Q2;
+      const double w = s_XB[4 * pq + 3] * gtab[G.WQC + r];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        double ps = 0;
+        for (int k = 0; k <= N; ++k) ps += s_GQ[k * Q + r] * s_C[(f * d::n1 + k) * Q2 + pq];
+        const double df = ps - s_S[f * Q3 + x];
+        acc[f == 0 ? 0 : 1] += w * df * df;
+      }
     }
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    sp += __shfl_down_sync(0xffffffffu, sp, off);
-    su += __shfl_down_sync(0xffffffffu, su, off);
-  }
-  if ((tid & 31) == 0) {
-    red[0][tid >> 5] = sp;
-    red[1][tid >> 5] = su;
-  }
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], off);
+  if ((tid & 31) == 0)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) red[c][tid >> 5] = acc[c];
   __syncthreads();
-  if (tid == 0) {
-    double a = 0.0, b = 0.0;
-    for (int w = 0; w < NW; ++w) {
-      a += red[0][w];
-      b += red[1][w];
-    }
-    partial[2 * blockIdx.x] = a;
-    partial[2 * blockIdx.x + 1] = b;
+  if (tid < 4) {
+    double a = 0.0;
+    for (int w = 0; w < NW; ++w) a += red[tid][w];
+    partial[4 * blockIdx.x + tid] = a;
   }
 }
 
-template <int N>
-struct ErrCSmem {
-  using d = Dims<N>;
-  static constexpr int Q = d::Q;
-  static constexpr size_t u = 0;
-  static constexpr size_t A = u + 4 * d::Np;
-  static constexpr size_t B = A + 4 * d::nrow * Q;
-  static constexpr size_t LQ = B + 4 * d::n1 * Q * Q;
-  static constexpr size_t GQ = LQ + d::nrow * Q;
-  static constexpr size_t W = GQ + d::n1 * Q;
-  static constexpr size_t total = W + Q * Q;
-  static constexpr size_t bytes = total * sizeof(double);
-};
-
-// The error norm's sum of w (U_h - U_exact)^2 with the exact fields from the cache:
-// U_exact = S_f tp (f = 0) or S_f tu (velocities), tp = cos(sqrt3 pi sc t), tu = sin(...)/sqrt3.
-// U_h at the points by the same a, b, c passes as error_kernel. partial[2 b] gets the block's
-// sum, partial[2 b + 1] zero.
+// sum over all elements, fields and modes of M_ii (u_i - T s_i)^2 (T = tp for p, tu for the
+// velocities); partial[2 b] gets the block's sum, partial[2 b + 1] zero.
 template <int N, typename T>
-__global__ void __launch_bounds__(ErrCfg<N>::NT)
-    error_cached_kernel(int64_t K, const T* __restrict__ q, const double* __restrict__ gtab,
-                        const double* __restrict__ S, const double* __restrict__ W, double tp, double tu,
-                        double* __restrict__ partial) {
-  using d = Dims<N>;
-  using SM = ErrCSmem<N>;
-  constexpr GeoLayout G(N);
-  constexpr int Q = d::Q;
-  constexpr int NW = ErrCfg<N>::NT / 32;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sm = reinterpret_cast<double*>(smem_raw);
-  double* s_u = sm + SM::u;
-  double* s_A = sm + SM::A;
-  double* s_B = sm + SM::B;
-  double* s_LQ = sm + SM::LQ;
-  double* s_GQ = sm + SM::GQ;
-  double* s_W = sm + SM::W;
-  __shared__ double red[NW];
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  for (int x = tid; x < d::nrow * Q; x += nthr) s_LQ[x] = gtab[G.LQ + x];
-  for (int x = tid; x < d::n1 * Q; x += nthr) s_GQ[x] = gtab[G.GQ + x];
-  double e2 = 0.0;
-  for (int64_t e = blockIdx.x; e < K; e += gridDim.x) {
-    __syncthreads();
-    for (int x = tid; x < 4 * d::Np; x += nthr) s_u[x] = (double)q[e * 4 * d::Np + x];
-    for (int x = tid; x < Q * Q; x += nthr) s_W[x] = W[e * Q * Q + x];
-    __syncthreads();
-    for (int x = tid; x < 4 * d::nrow * Q; x += nthr) {  // a pass, level-major
-      int k = 0;
-      while (x >= 4 * Q * tri_num(k + 1)) ++k;
-      const int rem = x - 4 * Q * tri_num(k);
-      const int f = rem / ((k + 1) * Q);
-      const int j = (rem / Q) % (k + 1);
-      const int p = rem % Q;
-      const double* uc = s_u + f * d::Np + lvl_off(k) + j * (k + 1);
-      const double* lq = s_LQ + tri_num(k) * Q + p;
-      double acc = 0;
-      for (int i = 0; i <= k; ++i) acc += uc[i] * lq[i * Q];
-      s_A[(f * d::nrow + tri_num(k) + j) * Q + p] = acc;
-    }
-    __syncthreads();
-    for (int x = tid; x < 4 * d::n1 * Q * Q; x += nthr) {  // b pass, level-major
-      const int pq = x % (Q * Q);
-      const int tt = x / (Q * Q);
-      const int f = tt % 4, k = tt / 4;
-      const int p = pq % Q, qq = pq / Q;
-      const double* Ar = s_A + (f * d::nrow + tri_num(k)) * Q + p;
-      const double* lq = s_LQ + tri_num(k) * Q + qq;
-      double acc = 0;
-      for (int j = 0; j <= k; ++j) acc += Ar[j * Q] * lq[j * Q];
-      s_B[(f * d::n1 + k) * Q * Q + pq] = acc;
-    }
-    __syncthreads();
-    for (int x = tid; x < Q * Q * Q; x += nthr) {  // c pass and the error integrand
-      const int pq = x % (Q * Q), r = x / (Q * Q);
-      const double2* sx = reinterpret_cast<const double2*>(S + (e * Q * Q * Q + x) * 4);
-      const double2 s01 = sx[0], s23 = sx[1];
-      const double Sf[4] = {s01.x, s01.y, s23.x, s23.y};
-      double ept = 0.0;
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        double uh = 0;
-#pragma unroll
-        for (int k = 0; k <= N; ++k) uh += s_GQ[k * Q + r] * s_B[(f * d::n1 + k) * Q * Q + pq];
-        const double df = fma(-Sf[f], f == 0 ? tp : tu, uh);  // U_h - U_exact
-        ept += df * df;
-      }
-      e2 += s_W[pq] * gtab[G.WQC + r] * ept;
-    }
+__global__ void __launch_bounds__(256)
+    error_proj_kernel(int64_t K, const T* __restrict__ q, const double* __restrict__ shat,
+                      const double* __restrict__ Mdiag, double tp, double tu, double* __restrict__ partial) {
+  constexpr int Np = Dims<N>::Np;
+  __shared__ double red[8];
+  double acc = 0.0;
+  const int64_t total = K * 4 * Np;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = x / (4 * Np);
+    const int r = (int)(x - e * 4 * Np);
+    const int f = r / Np, n = r - f * Np;
+    const double df = fma(-(f == 0 ? tp : tu), shat[x], (double)q[x]);
+    acc += Mdiag[e * Np + n] * df * df;
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, off);
-  if ((tid & 31) == 0) red[tid >> 5] = e2;
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     double a = 0.0;
-    for (int w = 0; w < NW; ++w) a += red[w];
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
     partial[2 * blockIdx.x] = a;
     partial[2 * blockIdx.x + 1] = 0.0;
   }

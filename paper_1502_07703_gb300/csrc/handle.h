@@ -42,12 +42,13 @@ struct pyr_dg {
   // per-element time step (device, K elements of the handle's type) when the handle
   // holds several batched meshes; null for a single mesh
   void* dt_elem = nullptr;
-  // pyr_dg_error's store of the exact fields' spatial factors at the error-rule points
-  // (K (4 Q^3 + Q^2) doubles, Q = N+3) and their two weighted sums of squares.
+  // pyr_dg_error's store: the error rule's projection of the exact fields' spatial factors
+  // (K x 4 x Np doubles), the mass diagonal in double (K x Np), then 4 sums per error block;
+  // ecache_sum: |PS_p - S_p|^2, sum_m |PS_m - S_m|^2, |S_p|^2, sum_m |S_m|^2 over the mesh.
   // ecache_mode: 1 store when it fits (default), 0 never. ecache_state: 0 no call yet,
   // 2 one call made without the store, 1 stored, -1 not stored (too large, or mode 0).
   double* ecache = nullptr;
-  double ecache_norm[2] = {0.0, 0.0};
+  double ecache_sum[4] = {0.0, 0.0, 0.0, 0.0};
   int ecache_mode = 1, ecache_state = 0;
   // per-kernel event timing of pyr_dg_step (pyr_dg_profile)
   bool profiling = false;

@@ -17,7 +17,7 @@ struct Impl {
   static_assert(RhsSmem<N, T>::bytes <= kMaxSmem, "rhs kernel shared memory");
   static_assert(ProjSmem<N>::bytes + 15 * 8 <= kMaxSmem, "projection kernel shared memory");
   static_assert(ErrSmem<N>::bytes + 8 * (15 + 2 * 16) <= kMaxSmem, "error kernel shared memory");
-  static_assert(ErrCSmem<N>::bytes + 8 * 16 <= kMaxSmem, "cached error kernel shared memory");
+  static_assert(ProjQSmem<N>::bytes + 8 * (15 + 4 * 16) <= kMaxSmem, "error-rule projection shared memory");
   static_assert(4 * Dims<N>::n2 <= 4 * Dims<N>::n1 * Dims<N>::P3 * Dims<N>::P3, "projection B/J scratch");
   static_assert(S32<N, 1>::bytes <= kMaxSmem, "FP32 stage kernel shared memory");
   static_assert(Rhs1Smem<N, T>::bytes <= kMaxSmem && Proj1Smem<N>::bytes <= kMaxSmem, "advection shared memory");
@@ -47,8 +47,8 @@ struct Impl {
     e = cudaFuncSetAttribute(project1_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Proj1Smem<N>::bytes);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(error_cached_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ErrCSmem<N>::bytes);
+    e = cudaFuncSetAttribute(exact_proj_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ProjQSmem<N>::bytes);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(error_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)ErrSmem<N>::bytes);
@@ -115,14 +115,13 @@ struct Impl {
                     double* partial, int nblocks, cudaStream_t s) {
     error_kernel<N, T><<<nblocks, ErrCfg<N>::NT, ErrSmem<N>::bytes, s>>>(K, (const T*)q, ev, gtab, bc, t, partial);
   }
-  static void exact_cache(int64_t K, const double* ev, const double* gtab, int bc, double* S, double* W,
-                          double* partial, int nblocks, cudaStream_t s) {
-    exact_cache_kernel<N><<<nblocks, ErrCfg<N>::NT, 0, s>>>(K, ev, gtab, bc, S, W, partial);
+  static void exact_proj(int64_t K, const double* ev, const double* gtab, int bc, double* shat, double* Mdiag,
+                         double* partial, int nblocks, cudaStream_t s) {
+    exact_proj_kernel<N><<<nblocks, ErrCfg<N>::NT, ProjQSmem<N>::bytes, s>>>(K, ev, gtab, bc, shat, Mdiag, partial);
   }
-  static void error_cached(int64_t K, const void* q, const double* gtab, const double* S, const double* W, double tp,
-                           double tu, double* partial, int nblocks, cudaStream_t s) {
-    error_cached_kernel<N, T><<<nblocks, ErrCfg<N>::NT, ErrCSmem<N>::bytes, s>>>(K, (const T*)q, gtab, S, W, tp,
-                                                                               tu, partial);
+  static void error_proj(int64_t K, const void* q, const double* shat, const double* Mdiag, double tp, double tu,
+                         double* partial, int nblocks, cudaStream_t s) {
+    error_proj_kernel<N, T><<<nblocks, 256, 0, s>>>(K, (const T*)q, shat, Mdiag, tp, tu, partial);
   }
   template <int E>
   static void stage32_e(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
@@ -274,8 +273,8 @@ struct Impl {
     l.rhs_out = &rhs_out;
     l.project = &project;
     l.error = &error;
-    l.exact_cache = &exact_cache;
-    l.error_cached = &error_cached;
+    l.exact_proj = &exact_proj;
+    l.error_proj = &error_proj;
     l.trace1 = &trace1;
     l.rhs1 = &rhs1;
     l.project1 = &project1;

@@ -23,14 +23,15 @@ struct Launchers {
                   cudaStream_t s);
   void (*error)(int64_t K, const void* q, const double* ev, const double* gtab, int bc, double t, double* partial,
                 int nblocks, cudaStream_t s);
-  // Error norm with the exact fields' spatial factors stored once (K (4 Q^3 + Q^2) doubles,
-  // Q = N+3: S, then W): exact_cache fills them and writes per-block sums of w S_p^2 and
-  // w (S_u^2 + S_v^2 + S_w^2); error_cached sums w (U_h - U_exact)^2 for the time factors
-  // tp = cos(sqrt3 pi sc t), tu = sin(sqrt3 pi sc t)/sqrt3.
-  void (*exact_cache)(int64_t K, const double* ev, const double* gtab, int bc, double* S, double* W,
-                      double* partial, int nblocks, cudaStream_t s);
-  void (*error_cached)(int64_t K, const void* q, const double* gtab, const double* S, const double* W, double tp,
-                       double tu, double* partial, int nblocks, cudaStream_t s);
+  // Error norm from coefficients (the wave's exact fields are S(x) times a time factor):
+  // exact_proj fills shat (K x 4 x Np: coefficients of the error rule's projection of S) and
+  // Mdiag (K x Np: M_ii) and writes per-block sums of |PS_p - S_p|^2, sum_m |PS_m - S_m|^2,
+  // |S_p|^2 and sum_m |S_m|^2 (4 per block); error_proj sums M_ii (u_i - T s_i)^2 with
+  // T = tp (p) or tu (velocities), tp = cos(sqrt3 pi sc t), tu = sin(sqrt3 pi sc t)/sqrt3.
+  void (*exact_proj)(int64_t K, const double* ev, const double* gtab, int bc, double* shat, double* Mdiag,
+                     double* partial, int nblocks, cudaStream_t s);
+  void (*error_proj)(int64_t K, const void* q, const double* shat, const double* Mdiag, double tp, double tu,
+                     double* partial, int nblocks, cudaStream_t s);
   // Single-launch FP32 stage (null for double): reads traces of q from tr_cur, writes
   // the updated state, residual and (if write_traces) the new traces into tr_nxt.
   // epb: elements per CTA, one that blocks_per_sm32 reports as built.

@@ -326,17 +326,19 @@ def test_error_norm_fine_meshes(torch_cuda, nx, bc):
         np.testing.assert_allclose(err, err_or, rtol=1e-12)
 
 
-@pytest.mark.parametrize("precision,N", [("f64", 3), ("f32", 3), ("f64", 1), ("f64", 5), ("f32", 7)])
+@pytest.mark.parametrize("precision,N", [("f64", 3), ("f32", 3), ("f64", 1), ("f64", 5), ("f32", 7), ("f64", 4)])
 def test_error_norm_store_matches_direct(torch_cuda, precision, N):
-    """The stored spatial factors give the same error norm as the direct kernel at several
-    times (the time factors come from the host), and the store takes the device memory the
-    header states and gives it back when switched off."""
+    """The error norm from coefficients (the error rule's projection of the exact fields'
+    spatial factors, stored at the second call) equals the direct kernel's at several times
+    (the time factors come from the host), and the store takes the device memory the header
+    states and gives it back when switched off."""
     import torch
-    v, e = make_pyramid_mesh(6 if N <= 5 else 3, delta=0.05, seed=7)
+    # 16^3 hexes at N = 4: a store of 54 MB, large enough for the device-memory checks
+    # (small stores come out of already-mapped pages)
+    v, e = make_pyramid_mesh(16 if N == 4 else 6 if N <= 5 else 3, delta=0.05, seed=7)
     with _solver(v, e, N, precision=precision) as s:
         U = random_state(s.K, s.Np, 31).astype(s.np_dtype)
-        Q = N + 3
-        store = s.K * (4 * Q ** 3 + Q ** 2) * 8
+        store = s.K * 5 * s.Np * 8
         for t in (0.0, 0.37, 1.9):
             s.set_state(U, t=t)
             s.set_error_cache(False)
@@ -344,14 +346,33 @@ def test_error_norm_store_matches_direct(torch_cuda, precision, N):
             free0 = torch.cuda.mem_get_info()[0]
             s.set_error_cache(True)
             np.testing.assert_allclose(s.error(), direct, rtol=1e-12)  # no store at one call
-            assert free0 - torch.cuda.mem_get_info()[0] < store
+            big = store >= 16 << 20
+            assert not big or free0 - torch.cuda.mem_get_info()[0] < store
             stored = s.error()
             free1 = torch.cuda.mem_get_info()[0]
-            assert free0 - free1 >= store, (free0, free1, store)
+            assert not big or free0 - free1 >= store, (free0, free1, store)
             np.testing.assert_allclose(s.error(), direct, rtol=1e-12)
             np.testing.assert_allclose(stored, direct, rtol=1e-12)
         s.set_error_cache(False)
-        assert torch.cuda.mem_get_info()[0] - free1 >= store
+        assert not big or torch.cuda.mem_get_info()[0] - free1 >= store
+
+
+@pytest.mark.parametrize("bc", ["wall", "free"])
+def test_error_norm_store_converged_state(torch_cuda, bc):
+    """On an evolved standing wave the error is small against the fields, and both of its
+    parts matter: sum M (u - T s)^2 and the projection error T^2 |PS - S|^2. The stored path
+    and the direct kernel agree to the digits that survive the cancellation in U_h - U_ex."""
+    v, e = make_pyramid_mesh(8, delta=0.05, seed=3, domain=_domain(bc))
+    N = 3
+    with _solver(v, e, N, bc=bc) as s:
+        dt = s.dt_cfl(0.5)
+        s.project(0.0)
+        s.step(20, dt)
+        direct = s.error()
+        s.error()  # stores
+        stored = s.error()
+    assert 1e-9 < direct[1] < 1e-4, direct
+    np.testing.assert_allclose(stored, direct, rtol=1e-6)
 
 
 @pytest.mark.parametrize("nx,N", [(32, 5), (16, 7)])
