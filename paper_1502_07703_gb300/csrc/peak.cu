@@ -1,5 +1,5 @@
 // pyr_dg_fma_peak: measured FMA throughput of the current GPU, the ALU
-// ceiling against which the double-precision stage kernels are judged.
+// ceiling against which the double-precision stage kernels are measured.
 #include <cuda_runtime.h>
 
 #include <cstdio>
