@@ -44,8 +44,8 @@ SAMPLE_NX = 8  # oracle sample: 8^3 hexes x 6 = 3072 pyramids, same N, perturbat
 
 
 def _hbm_peak():
-    """Measured copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json beside this file),
-    else the earlier single measurement of 6.8 TB/s, with which one it is."""
+    """Measured HBM copy bandwidth of the GB300 (MEASURED_PEAKS.json beside this file),
+    else an earlier single measurement of 6.8 TB/s, with which one it is."""
     try:
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
             return float(json.load(fh)["hbm_gbs"]), "measured"
