@@ -105,6 +105,7 @@ def test_raw_abi_null_and_range_checks():
     assert L.pyr_dg_setup(None, 0, None, 0, 3, None, ctypes.byref(h)) == -1
     assert L.pyr_dg_step(None, 1, 0.1) == -1
     assert L.pyr_dg_error(None, None, None) == -1
+    assert L.pyr_dg_set_error_cache(None, 1) == -1
     assert b"null" in L.pyr_dg_last_error()
     x = np.empty(4)
     assert L.pyr_dg_host_gauss_jacobi(0, 0.0, 0.0, x.ctypes.data_as(binding._c_dp), x.ctypes.data_as(binding._c_dp)) == -1
