@@ -138,8 +138,13 @@ def _face_tangents(f, Jac):
 class PyramidDG:
     """Dense-matrix DG discretisation on a pyramid mesh (state arrays (K, 4, Np), psi basis)."""
 
-    def __init__(self, vertices, EToV, N, tau=1.0, bc="wall", chunk=512, periodic=None):
+    def __init__(self, vertices, EToV, N, tau=1.0, bc="wall", chunk=512, periodic=None, threads=1):
         self.N = int(N)
+        # threads > 1: the per-element contractions of traces / residual / rhs run on element
+        # chunks in a thread pool (numpy releases the GIL in einsum); each element's arithmetic
+        # is the same as with one thread. Used to time the oracle on all host cores.
+        self.threads = max(1, int(threads))
+        self._pool = None
         self.Np = num_modes(self.N)
         self.tau = float(tau)
         self.bc = bc
@@ -226,9 +231,21 @@ class PyramidDG:
         self.interior = inter
 
     # ------------------------------------------------------------------ operators
+    def _per_element(self, fn, *arrays):
+        """fn(*arrays) where every array's first axis runs over the elements: on one thread, or
+        on contiguous element chunks in the thread pool, concatenated in element order."""
+        if self.threads == 1 or self.K < 2 * self.threads:
+            return fn(*arrays)
+        if self._pool is None:
+            from concurrent.futures import ThreadPoolExecutor
+            self._pool = ThreadPoolExecutor(self.threads)
+        bounds = np.linspace(0, self.K, self.threads + 1).astype(int)
+        parts = self._pool.map(lambda i: fn(*(a[bounds[i]:bounds[i + 1]] for a in arrays)), range(self.threads))
+        return np.concatenate(list(parts), axis=0)
+
     def traces(self, U):
         """Values of the four fields at every face point, (K, 5, nf, 4)."""
-        return np.einsum("fqn,kcn->kfqc", self.Vf, U)
+        return self._per_element(lambda u: np.einsum("fqn,kcn->kfqc", self.Vf, u), U)
 
     def exterior(self, Uf):
         """Neighbour (or boundary mirror) values at every face point, same shape as Uf."""
@@ -267,14 +284,18 @@ class PyramidDG:
         u = U[:, 1:]
         Fp, Fu, _, _ = self.fluxes(U)
         W = self.fw[None] * self.sJ  # (K, 5, nf)
-        out = np.empty_like(U)
-        out[:, 0] = np.einsum("kmij,kmj->ki", self.S, u) + np.einsum("fqi,kfq->ki", self.Vf, W * Fp)
-        out[:, 1:] = np.einsum("kmij,kj->kmi", self.S, p) + np.einsum("fqi,kfqm->kmi", self.Vf, W[..., None] * Fu)
-        return out
+
+        def part(S, p, u, WFp, WFu):
+            out = np.empty((S.shape[0],) + U.shape[1:])
+            out[:, 0] = np.einsum("kmij,kmj->ki", S, u) + np.einsum("fqi,kfq->ki", self.Vf, WFp)
+            out[:, 1:] = np.einsum("kmij,kj->kmi", S, p) + np.einsum("fqi,kfqm->kmi", self.Vf, WFu)
+            return out
+
+        return self._per_element(part, self.S, p, u, W * Fp, W[..., None] * Fu)
 
     def rhs(self, U):
         """dU/dt = -M^{-1} (volume + surface terms), dense inverse per element."""
-        return -np.einsum("kij,kcj->kci", self.Minv, self.residual(U))
+        return self._per_element(lambda Mi, R: -np.einsum("kij,kcj->kci", Mi, R), self.Minv, self.residual(U))
 
     def lsrk4(self, U, dt, nsteps):
         """Advance nsteps of the 2N-storage RK4 with fixed dt; returns the new state."""
@@ -367,3 +388,46 @@ class PyramidDG:
         d2 = np.einsum("kq,kqc->", wJ, (A - B) ** 2)
         n2 = np.einsum("kq,kqc->", wJ, B ** 2)
         return np.sqrt(d2 / n2)
+
+    def worst_element_rel(self, A, B, elems=None):
+        """The worst element of two point-value arrays (K', Nc, 4) whose rows are the elements
+        `elems` (default: all K, in order): max over elements of the quadrature-weighted L2
+        difference on that element, divided by the larger of that element's norm of B and the
+        root-mean-square element norm of B over the rows.
+
+        A fault confined to one element (or one face of it) shows here at full size, where the
+        mesh-wide relative L2 dilutes it by the square root of the element count; the floor at
+        the mean element norm keeps elements where B nearly vanishes from dividing by ~0."""
+        J = self.J if elems is None else self.J[np.asarray(elems)]
+        if J.shape[0] != A.shape[0] or A.shape != B.shape:
+            raise ValueError("point arrays and element list disagree")
+        wJ = self.w[None, :] * J
+        d2 = np.einsum("kq,kqc->k", wJ, (A - B) ** 2)
+        n2 = np.einsum("kq,kqc->k", wJ, B ** 2)
+        floor = np.mean(n2)
+        return float(np.sqrt(np.max(d2 / np.maximum(n2, floor))))
+
+
+def phi_states_l2_diff(vertices, EToV, N, A, B, chunk=4096):
+    """Compare two semi-nodal coefficient states (K, 4, Np) of one mesh by their values at every
+    element's volume cubature points, without the dense element matrices (large meshes):
+    returns (mesh-wide quadrature-weighted relative L2 of A - B against B, worst element), the
+    worst element as in PyramidDG.worst_element_rel."""
+    ev = np.asarray(vertices, dtype=np.float64)[np.asarray(EToV)]
+    a, b, c, w = reference_rule(N + 1)
+    r, s, t = abc_to_rst(a, b, c)
+    V = phi(N, a, b, c)[0]
+    K = ev.shape[0]
+    d2 = np.empty(K)
+    n2 = np.empty(K)
+    for k0 in range(0, K, chunk):
+        sl = slice(k0, min(K, k0 + chunk))
+        _, Jac = map_points(ev[sl], r, s, t)
+        wJ = w[None, :] * np.linalg.det(Jac)
+        Av = np.einsum("qn,kcn->kqc", V, np.asarray(A[sl], dtype=np.float64))
+        Bv = np.einsum("qn,kcn->kqc", V, np.asarray(B[sl], dtype=np.float64))
+        d2[sl] = np.einsum("kq,kqc->k", wJ, (Av - Bv) ** 2)
+        n2[sl] = np.einsum("kq,kqc->k", wJ, Bv ** 2)
+    rel = float(np.sqrt(d2.sum() / n2.sum()))
+    worst = float(np.sqrt(np.max(d2 / np.maximum(n2, np.mean(n2)))))
+    return rel, worst

@@ -232,3 +232,60 @@ def test_spectral_radius_fit_and_cfl_stability(N):
         res = LSRK_A[s] * res + dt * lam * y
         y = y + LSRK_B[s] * res
     assert np.max(np.abs(y)) <= 1.0 + 1e-12
+
+
+def _golden_cfl_constants():
+    """C_N of the Sec. 4.3 spectral-radius fit, read from tests/golden/spectral_radius_constants.txt
+    (tabulated as the numerator over 3)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "spectral_radius_constants.txt")
+    out = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            n, num = line.split()
+            out[int(n)] = int(num) / 3.0
+    return out
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
+def test_dt_cfl_uses_the_papers_constant(N):
+    """dt = CFL / (C_N max_K |dK|/|K|) with C_N from the golden table, on unperturbed meshes,
+    where every pyramid (a cube face as base, the cube centre as apex) has |K| = h^3/6 and
+    |dK| = h^2 (1 + sqrt 2) in closed form, so max |dK|/|K| = 6 (1 + sqrt 2) / h. A slip in the
+    oracle's constant (say (N+2) for (N+3)) or in its area or volume sums fails here."""
+    CN = _golden_cfl_constants()
+    assert sorted(CN) == list(range(1, 8))
+    for n_hex in (1, 2):
+        v, e = make_pyramid_mesh(n_hex, delta=0.0)
+        dg = PyramidDG(v, e, N)
+        aov = 6.0 * (1.0 + np.sqrt(2.0)) * n_hex
+        np.testing.assert_allclose(dg.volumes(), 1.0 / (6 * n_hex ** 3), rtol=1e-13)
+        np.testing.assert_allclose(dg.surface_areas(), (1.0 + np.sqrt(2.0)) / n_hex ** 2, rtol=1e-13)
+        for cfl in (0.5, 0.25):
+            np.testing.assert_allclose(dg.dt_cfl(cfl), cfl / (CN[N] * aov), rtol=1e-13)
+
+
+def test_worst_element_measure_sees_a_single_element_fault():
+    """The worst-element parity measure at full size for a fault in one element, where the
+    mesh-wide relative L2 is diluted by about sqrt(K); the chunked large-mesh comparison gives
+    the same two numbers as the dense oracle's."""
+    from oracle.dg import phi_states_l2_diff
+    from paper_1502_07703_gb300.mesh import random_state
+    v, e = make_pyramid_mesh(2, delta=0.05, seed=0)
+    N = 3
+    dg = PyramidDG(v, e, N)
+    B = random_state(dg.K, dg.Np, 5)
+    A = B.copy()
+    A[17, 2] *= 1.0 + 1e-4  # one field of one element off by 1e-4
+    Av, Bv = dg.values_phi(A), dg.values_phi(B)
+    rel, worst = dg.rel_l2_points(Av, Bv), dg.worst_element_rel(Av, Bv)
+    assert worst > 3e-5 and rel < worst / 3, (rel, worst)
+    assert dg.worst_element_rel(Bv, Bv) == 0.0
+    r2, w2 = phi_states_l2_diff(v, e, N, A, B, chunk=5)
+    np.testing.assert_allclose([r2, w2], [rel, worst], rtol=1e-12)
+    # a single row with its element index gives that element's own relative difference
+    w1 = dg.worst_element_rel(Av[17:18], Bv[17:18], elems=[17])
+    wJ = dg.w * dg.J[17]
+    own = np.sqrt(np.einsum("q,qc->", wJ, (Av[17] - Bv[17]) ** 2) / np.einsum("q,qc->", wJ, Bv[17] ** 2))
+    np.testing.assert_allclose(w1, own, rtol=1e-12)
