@@ -61,6 +61,7 @@ enum { PYR_DG_F64 = 0, PYR_DG_F32 = 1 };
 enum { PYR_DG_BC_WALL = 0, PYR_DG_BC_FREE = 1 };
 enum { PYR_DG_HOST = 0, PYR_DG_DEVICE = 1 };
 enum { PYR_DG_WAVE = 0, PYR_DG_ADVECTION = 1 };
+enum { PYR_DG_MODAL = 0, PYR_DG_NODAL = 1 };
 
 typedef struct pyr_dg pyr_dg; /* opaque handle, owned by the library */
 
@@ -82,11 +83,28 @@ typedef struct pyr_dg_opts {
   int periodic;   /* 1: the box [box_lo, box_hi]^3 is periodic: faces on opposite boundary
                      planes are neighbours (their vertices must coincide modulo the period) */
   double box_lo, box_hi;
+  int basis;      /* PYR_DG_MODAL: the state holds semi-nodal coefficients (layout above).
+                     PYR_DG_NODAL: the nodal variant of Sec. 4.4.1 (wave equation, F64
+                     only): the state holds each field's values at Np nodes, the
+                     Lagrange basis at them spans the same space, so the discrete
+                     solution is the same function. Nodes (pyr_dg_host_nodal_points):
+                     layer m = 0..N at c = the m-th of the N+1 Gauss-Lobatto-Legendre
+                     (GLL) points, carrying the (N+1-m) x (N+1-m) GLL grid in (a, b)
+                     (the apex layer one node at (0, 0, 1)); ordered by layer, then b,
+                     then a. M^{-1} is applied as V M_phi^{-1} V^T, V the Vandermonde of
+                     the semi-nodal basis at the nodes; triangle faces are integrated
+                     with the nodal face mass matrix, the (possibly non-planar) base with
+                     its Gauss-Legendre rule. */
 } pyr_dg_opts;
 
 /* Fill *opts with: F64, wall, tau = 1, stream NULL, device -1, wave equation,
- * beta = (1, 0, 0), not periodic, box [0, 1]. */
+ * beta = (1, 0, 0), not periodic, box [0, 1], modal basis. */
 void pyr_dg_default_opts(pyr_dg_opts* opts);
+
+/* The nodal set of the nodal variant at degree N (host only, no GPU needed):
+ * abc receives Np x 3 doubles, the collapsed coordinates (a, b, c) of each node
+ * in state order (see pyr_dg_opts.basis). */
+int pyr_dg_host_nodal_points(int N, double* abc);
 
 /* Build a solver for one mesh (Sec. 2 vertex maps, Sec. 4.1 cubature).
  * vertices: host, Nv x 3 doubles, row-major (copied).
@@ -144,9 +162,13 @@ int pyr_dg_rhs(pyr_dg* h, const void* q_dev, void* rhs_dev);
  *    PYR_DG_NOALLOC_SCRATCH_BYTES (8 MiB: e.g. 2097 pyramids at N = 4 in
  *    double); larger handles get PYR_DG_ERR_BAD_ARG and a message.
  *  - The array exists on every GPU that loads the library, until the process
- *    exits. The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current and caches it; make that
- *    first call before any stream capture.
+ *    exits. pyr_dg_setup looks up the array's device address
+ *    (cudaGetSymbolAddress) with the handle's device current and caches it
+ *    per device; under lazy module loading that lookup is also when the
+ *    driver places the array on the device, so it happens in setup, where
+ *    allocating is allowed, and never inside this call for a handle whose
+ *    setup succeeded. (Only if that lookup failed in setup does this call
+ *    retry it; such a first call should come before any stream capture.)
  *  - Every call shares the one array per device and it keeps the last call's
  *    contents. Each call writes every entry it reads before reading it, so
  *    nothing needs clearing, but calls whose work overlaps on the GPU (other
@@ -178,6 +200,15 @@ int pyr_dg_error(pyr_dg* h, double* l2_abs, double* l2_rel);
  * pyr_dg_destroy. That call and later ones then read only the coefficients. Without
  * the store (the first call, or when it does not fit) the call evaluates U_h and the
  * exact fields at the error-rule points. Both give the same value up to rounding. */
+
+/* L2 distance between two states of this handle (device pointers, K x nf x Np
+ * elements of the handle's type, any may alias): d2 = sum over elements, fields
+ * and modes of M_ii (qa_i - qb_i)^2 and n2 = the same of M_ii qb_i^2, summed in
+ * double. The semi-nodal basis is orthogonal on every element (Lemma 3) and the
+ * volume rule integrates the mass matrix exactly, so these are the squared L2
+ * norms of the difference and of qb over the mesh, M_ii = 1 / (the stored
+ * M^{-1} entry). Either output pointer may be NULL. Synchronises. */
+int pyr_dg_l2_diff(pyr_dg* h, const void* qa_dev, const void* qb_dev, double* d2, double* n2);
 
 /* enable = 0: free the stored factors and evaluate the exact fields at every call;
  * enable != 0 (the default): store them at the second pyr_dg_error from now when

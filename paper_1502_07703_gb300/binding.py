@@ -20,6 +20,7 @@ PYR_DG_F64, PYR_DG_F32 = 0, 1
 PYR_DG_BC_WALL, PYR_DG_BC_FREE = 0, 1
 PYR_DG_HOST, PYR_DG_DEVICE = 0, 1
 PYR_DG_WAVE, PYR_DG_ADVECTION = 0, 1
+PYR_DG_MODAL, PYR_DG_NODAL = 0, 1
 ERRORS = {-1: "BAD_ARG", -2: "BAD_MESH", -3: "UNSUPPORTED_N", -4: "CUDA", -5: "NO_MEMORY"}
 
 _lib = None
@@ -43,6 +44,7 @@ class Opts(ctypes.Structure):
         ("periodic", ctypes.c_int),
         ("box_lo", ctypes.c_double),
         ("box_hi", ctypes.c_double),
+        ("basis", ctypes.c_int),
     ]
 
 
@@ -91,6 +93,8 @@ _SIGNATURES = {
     "pyr_dg_batch_stream": (ctypes.c_void_p, [_c_h]),
     "pyr_dg_batch_destroy": (None, [_c_h]),
     "pyr_dg_profile_read": (ctypes.c_int, [_c_h, _c_dp, _c_i64p, _c_dp, _c_i64p]),
+    "pyr_dg_l2_diff": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_void_p, _c_dp, _c_dp]),
+    "pyr_dg_host_nodal_points": (ctypes.c_int, [ctypes.c_int, _c_dp]),
 }
 
 
@@ -160,13 +164,24 @@ def fma_peak(precision="f64"):
     return out.value
 
 
+def host_nodal_points(N):
+    """(Np, 3) collapsed coordinates (a, b, c) of the nodal variant's nodes, in state order
+    (host-only builder query, no GPU needed)."""
+    Np = (N + 1) * (N + 2) * (2 * N + 3) // 6
+    out = np.empty((Np, 3))
+    _check(lib().pyr_dg_host_nodal_points(int(N), _ptr(out, ctypes.c_double)))
+    return out
+
+
 class Solver:
     """One mesh advanced by the library. State arrays are (K, 4, Np) in the
-    handle's precision, semi-nodal coefficients (layout in include/pyrdg.h)."""
+    handle's precision: semi-nodal coefficients, or with basis="nodal" the values at the
+    nodes of host_nodal_points (layout in include/pyrdg.h)."""
 
     def __init__(self, vertices, EToV, N, precision="f64", bc="wall", tau=1.0, stream=None, device=None,
-                 equation="wave", beta=(1.0, 0.0, 0.0), periodic=None):
-        """equation: "wave" (4 fields) or "advection" (1 field, needs periodic=(lo, hi); tau is alpha)."""
+                 equation="wave", beta=(1.0, 0.0, 0.0), periodic=None, basis="modal"):
+        """equation: "wave" (4 fields) or "advection" (1 field, needs periodic=(lo, hi); tau is alpha).
+        basis: "modal" (semi-nodal coefficients) or "nodal" (Sec. 4.4.1; wave, f64)."""
         import torch
 
         self._torch = torch
@@ -180,6 +195,7 @@ class Solver:
         o.bc = {"wall": PYR_DG_BC_WALL, "free": PYR_DG_BC_FREE}[bc]
         o.tau = float(tau)
         o.equation = {"wave": PYR_DG_WAVE, "advection": PYR_DG_ADVECTION}[equation]
+        o.basis = {"modal": PYR_DG_MODAL, "nodal": PYR_DG_NODAL}[basis]
         for m in range(3):
             o.beta[m] = float(beta[m])
         if periodic is not None:
@@ -207,6 +223,7 @@ class Solver:
         _check(lib().pyr_dg_num_fields(h, ctypes.byref(nf)))
         self.nf = nf.value
         self.equation = equation
+        self.basis = basis
         self.np_dtype = np.float64 if precision == "f64" else np.float32
         self.torch_dtype = torch.float64 if precision == "f64" else torch.float32
 
@@ -277,6 +294,17 @@ class Solver:
         a, r = ctypes.c_double(), ctypes.c_double()
         _check(lib().pyr_dg_error(self._h, ctypes.byref(a), ctypes.byref(r)))
         return a.value, r.value
+
+    def l2_diff(self, qa, qb):
+        """(L2 norm of qa - qb, L2 norm of qb) over the mesh for two device states of this handle
+        (torch CUDA tensors of the state's shape and dtype), from the diagonal mass matrix."""
+        for q in (qa, qb):
+            self._require_device(q)
+            if tuple(q.shape) != tuple(self.shape) or q.dtype != self.torch_dtype or not q.is_contiguous():
+                raise ValueError("l2_diff needs contiguous states of the handle's shape and dtype")
+        d2, n2 = ctypes.c_double(), ctypes.c_double()
+        _check(lib().pyr_dg_l2_diff(self._h, qa.data_ptr(), qb.data_ptr(), ctypes.byref(d2), ctypes.byref(n2)))
+        return float(np.sqrt(d2.value)), float(np.sqrt(n2.value))
 
     def set_error_cache(self, enable=True):
         """Store the exact fields' spatial factors for error() when they fit (the default),

@@ -64,6 +64,74 @@ using pyrdg::DeviceGuard;
 using pyrdg::fail;
 
 namespace {
+// Device address of pyr_dg_rhs_noalloc's static scratch on the current device (defined at
+// the end of this file); cached per device.
+cudaError_t noalloc_scratch_address(int device, void** out);
+}  // namespace
+
+namespace {
+// sum of M_ii (a_i - b_i)^2 and M_ii b_i^2 over a state (M_ii = 1 / invM), per block in double
+template <typename T>
+__global__ void __launch_bounds__(256)
+    l2_diff_kernel(int64_t total, int nf, int Np, const T* __restrict__ a, const T* __restrict__ b,
+                   const T* __restrict__ invM, double* __restrict__ partial) {
+  __shared__ double red[2][8];
+  double d2 = 0.0, n2 = 0.0;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = x / ((int64_t)nf * Np);
+    const int n = (int)(x % Np);
+    const double m = 1.0 / (double)invM[e * Np + n];
+    const double bv = (double)b[x], dv = (double)a[x] - bv;
+    d2 += m * dv * dv;
+    n2 += m * bv * bv;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    d2 += __shfl_down_sync(0xffffffffu, d2, off);
+    n2 += __shfl_down_sync(0xffffffffu, n2, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = d2;
+    red[1][threadIdx.x >> 5] = n2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      s0 += red[0][w];
+      s1 += red[1][w];
+    }
+    partial[2 * blockIdx.x] = s0;
+    partial[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+// out[e][f][i] = sum_n Mt[n Np + i] in[e][f][n] for every element and field: a per-element
+// change of basis of the nodal variant (Mt = V^T: coefficients to nodal values; Mt = V^{-T}:
+// the reverse).
+__global__ void __launch_bounds__(256)
+    nodal_apply_kernel(int64_t K, int Np, const double* __restrict__ Mt, const double* __restrict__ in,
+                       double* __restrict__ out) {
+  const int64_t total = K * 4 * Np;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(g % Np);
+    const double* v = in + (g - i);
+    double acc = 0.0;
+    for (int n = 0; n < Np; ++n) acc += Mt[(size_t)n * Np + i] * v[n];
+    out[g] = acc;
+  }
+}
+
+void nodal_apply(const pyr_dg* h, const double* Mt, const void* in, void* out) {
+  const int64_t total = h->K * 4 * h->Np;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+  nodal_apply_kernel<<<blocks, 256, 0, h->stream>>>(h->K, h->Np, Mt, (const double*)in, (double*)out);
+}
+
+// Offsets of V^T and V^{-T} in the nodal table (NodalDims layout: V, V^T, V^{-T}, ...).
+inline const double* nodal_VT(const pyr_dg* h) { return h->ntab + (size_t)h->Np * h->Np; }
+inline const double* nodal_VinvT(const pyr_dg* h) { return h->ntab + 2 * (size_t)h->Np * h->Np; }
+
 // Record an event pair slot around the next launch when profiling (kind 0 trace, 1 rhs).
 cudaError_t prof_begin(pyr_dg* h, int kind, size_t* slot) {
   if (!h->profiling) return cudaSuccess;
@@ -89,8 +157,9 @@ cudaError_t prof_end(pyr_dg* h, size_t slot) {
 void free_all(pyr_dg* h) {
   for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
   h->events.clear();
-  void* ptrs[] = {h->q,    h->res,  h->tr, h->geo,     h->gface, h->invM, h->tab,
-                  h->tabd, h->gtab, h->ev, h->partial, h->mapP, h->tr2, h->dt_elem, h->ecache};
+  void* ptrs[] = {h->q,    h->res,  h->tr,   h->geo,  h->gface,   h->invM,  h->tab,
+                  h->tabd, h->gtab, h->ev,   h->partial, h->mapP, h->tr2,   h->dt_elem,
+                  h->ecache, h->ntab, h->ntri, h->nmap};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -159,6 +228,24 @@ int enqueue_steps(pyr_dg* h, int nsteps, double dt) {
     h->tr_valid = true;
     return PYR_DG_OK;
   }
+  if (h->basis == PYR_DG_NODAL) {
+    // nodal variant: trace points of the nodal state (copies and the base interpolation),
+    // then the stage kernel, per stage
+    for (int n = 0; n < nsteps; ++n) {
+      for (int s = 0; s < 5; ++s) {
+        size_t slot = 0;
+        CUDA_TRY(prof_begin(h, 0, &slot));
+        h->L->nodal_trace(h->K, h->q, h->ntab, h->ntri, h->tr, h->stream);
+        CUDA_TRY(prof_end(h, slot));
+        CUDA_TRY(prof_begin(h, 1, &slot));
+        h->L->nodal_rhs(h->K, h->q, h->q, h->res, h->tr, h->nmap, h->geo, h->gface, h->invM, h->tab, h->ntab,
+                        h->ntri, h->bc, h->tau, kRkA[s], kRkB[s], dt, 1, h->stream);
+        CUDA_TRY(prof_end(h, slot));
+      }
+    }
+    CUDA_TRY(cudaGetLastError());
+    return PYR_DG_OK;
+  }
   // FP64: the trace kernel and the fused stage kernel per stage (a fused form that also
   // interpolates the new state runs slower: its shared memory caps the resident CTAs)
   for (int n = 0; n < nsteps; ++n) {
@@ -194,6 +281,7 @@ void pyr_dg_default_opts(pyr_dg_opts* o) {
   o->periodic = 0;
   o->box_lo = 0.0;
   o->box_hi = 1.0;
+  o->basis = PYR_DG_MODAL;
 }
 
 const char* pyr_dg_last_error(void) { return g_err.c_str(); }
@@ -202,6 +290,15 @@ int pyr_dg_host_gauss_jacobi(int n, double alpha, double beta, double* x, double
   if (!x || !w) return fail(PYR_DG_ERR_BAD_ARG, "null output pointer");
   if (pyrdg::gauss_jacobi(n, alpha, beta, x, w) != 0)
     return fail(PYR_DG_ERR_BAD_ARG, "gauss_jacobi: need 1 <= n <= 64 and alpha, beta > -1");
+  return PYR_DG_OK;
+}
+
+int pyr_dg_host_nodal_points(int N, double* abc) {
+  if (!abc) return fail(PYR_DG_ERR_BAD_ARG, "null output pointer");
+  if (N < PYR_DG_MIN_N || N > PYR_DG_MAX_N) return fail(PYR_DG_ERR_UNSUPPORTED_N, "N = %d unsupported", N);
+  pyrdg::NodalTables nt;
+  if (pyrdg::build_nodal(N, nt) != 0) return fail(PYR_DG_ERR_UNSUPPORTED_N, "nodal set build failed for N = %d", N);
+  std::memcpy(abc, nt.nodes.data(), nt.nodes.size() * sizeof(double));
   return PYR_DG_OK;
 }
 
@@ -255,6 +352,9 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   if (o.equation == PYR_DG_ADVECTION &&
       !(std::isfinite(o.beta[0]) && std::isfinite(o.beta[1]) && std::isfinite(o.beta[2])))
     return fail(PYR_DG_ERR_BAD_ARG, "beta must be finite");
+  if (o.basis != PYR_DG_MODAL && o.basis != PYR_DG_NODAL) return fail(PYR_DG_ERR_BAD_ARG, "unknown basis");
+  if (o.basis == PYR_DG_NODAL && (o.precision != PYR_DG_F64 || o.equation != PYR_DG_WAVE))
+    return fail(PYR_DG_ERR_BAD_ARG, "the nodal basis is implemented for the wave equation in double precision");
   const int n1 = N + 1, n2 = n1 * n1, Nfc = 5 * n2, Np = pyrdg::num_modes(N);
   if (K * (int64_t)Nfc > 0x7fffffffLL) return fail(PYR_DG_ERR_BAD_ARG, "K * Nfc exceeds int32 face indexing");
 
@@ -289,6 +389,43 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   std::vector<int32_t> map32((size_t)K * Nfc);
   for (size_t g = 0; g < map32.size(); ++g) map32[g] = (int32_t)map64[g];
 
+  // ---- nodal variant: tables and the trace-point matching (base Gauss-Legendre points from the
+  // face cubature matching; triangle-face nodes from the matched faces' orientation)
+  pyrdg::NodalTables NT;
+  std::vector<int32_t> nmap;
+  const pyrdg::Launchers* Lsel = pyrdg::get_launchers(N, o.precision);
+  const int ntr = o.basis == PYR_DG_NODAL ? Lsel->nodal_ntr : 0;
+  if (o.basis == PYR_DG_NODAL) {
+    if (pyrdg::build_nodal(N, NT) != 0) return fail(PYR_DG_ERR_UNSUPPORTED_N, "nodal set build failed for N = %d", N);
+    const int nT = NT.nT;
+    std::vector<int> lay(n1 + 1, 0);  // first local node of each layer on a triangle face
+    for (int m = 0; m < n1; ++m) lay[m + 1] = lay[m] + (n1 - m);
+    nmap.resize((size_t)K * ntr);
+    for (int64_t e = 0; e < K; ++e) {
+      for (int g = 0; g < n2; ++g) {
+        const int64_t gq = map64[(size_t)(e * Nfc + g)];
+        const int64_t en = gq / Nfc, gn = gq % Nfc;
+        if (gn >= n2) return fail(PYR_DG_ERR_BAD_MESH, "element %lld: base face matched to a triangle", (long long)e);
+        nmap[(size_t)(e * ntr + g)] = (int32_t)(en * ntr + gn);
+      }
+      for (int f = 1; f <= 4; ++f) {
+        const int64_t gq = map64[(size_t)(e * Nfc + f * n2)];  // the face's point (edge 0, height 0)
+        const int64_t en = gq / Nfc;
+        const int fn = (int)((gq % Nfc) / n2), idxn = (int)((gq % Nfc) % n2);
+        const bool self = gq == e * Nfc + f * n2;
+        if (!self && fn == 0) return fail(PYR_DG_ERR_BAD_MESH, "element %lld: triangle matched to a base", (long long)e);
+        const bool rev = (idxn % n1) != 0;  // edge reversal (the apex is shared)
+        for (int m = 0; m < n1; ++m)
+          for (int t = 0; t < n1 - m; ++t) {
+            const int j = lay[m] + t;
+            const int64_t own = e * ntr + n2 + (int64_t)(f - 1) * nT + j;
+            const int jn = lay[m] + (rev ? n1 - m - 1 - t : t);
+            nmap[(size_t)own] = self ? (int32_t)own : (int32_t)(en * ntr + n2 + (int64_t)(fn - 1) * nT + jn);
+          }
+      }
+    }
+  }
+
   pyr_dg* h = new (std::nothrow) pyr_dg();
   if (!h) return fail(PYR_DG_ERR_NO_MEMORY, "host allocation failed");
   h->N = N;
@@ -306,7 +443,9 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   h->tsize = o.precision == PYR_DG_F64 ? 8 : 4;
   h->stream = (cudaStream_t)o.stream;
   h->max_aov = max_aov;
-  h->L = pyrdg::get_launchers(N, o.precision);
+  h->L = Lsel;
+  h->basis = o.basis;
+  h->ntr = ntr;
   if (o.device >= 0) {
     h->device = o.device;
   } else if (cudaGetDevice(&h->device) != cudaSuccess) {
@@ -344,6 +483,9 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
       {(void**)&h->partial, (size_t)h->err_blocks * 2 * 8},
       {(void**)&h->mapP, (size_t)K * Nfc * 4},
       {&h->tr2, h->use_stage32 ? (size_t)K * Nfc * 4 * ts : 0},
+      {(void**)&h->ntab, o.basis == PYR_DG_NODAL ? (size_t)h->L->nodal_ntab * 8 : 0},
+      {(void**)&h->ntri, o.basis == PYR_DG_NODAL ? (size_t)4 * NT.nT * 4 : 0},
+      {(void**)&h->nmap, o.basis == PYR_DG_NODAL ? (size_t)K * ntr * 4 : 0},
   };
   for (auto& a : allocs) {
     if (a.bytes == 0) continue;
@@ -377,6 +519,26 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->gtab, T.geo.data(), (size_t)G.size * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->ev, ev.data(), ev.size() * 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h->mapP, map32.data(), map32.size() * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && h->basis == PYR_DG_NODAL) {
+    // table layout of NodalDims: V, V^T, V^{-T}, triangle nodal mass, GLL -> GL interpolation
+    std::vector<double> nt;
+    nt.reserve((size_t)h->L->nodal_ntab);
+    nt.insert(nt.end(), NT.V.begin(), NT.V.end());
+    nt.insert(nt.end(), NT.VT.begin(), NT.VT.end());
+    nt.insert(nt.end(), NT.VinvT.begin(), NT.VinvT.end());
+    nt.insert(nt.end(), NT.Mtri.begin(), NT.Mtri.end());
+    nt.insert(nt.end(), NT.I1.begin(), NT.I1.end());
+    if (nt.size() != (size_t)h->L->nodal_ntab) {
+      e = cudaErrorInvalidValue;
+    } else {
+      std::vector<int32_t> tri(NT.tri_node.begin(), NT.tri_node.end());
+      e = cudaMemcpyAsync(h->ntab, nt.data(), nt.size() * 8, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->ntri, tri.data(), tri.size() * 4, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h->nmap, nmap.data(), nmap.size() * 4, cudaMemcpyHostToDevice, s);
+      // the host vectors must outlive the copies: the stream is synchronised below
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->q, 0, stateB, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->res, 0, stateB, s);
   if (e == cudaSuccess) {
@@ -388,6 +550,13 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
     free_all(h);
     delete h;
     return fail(PYR_DG_ERR_CUDA, "setup: %s", cudaGetErrorString(e));
+  }
+  // pyr_dg_rhs_noalloc's static scratch: fetch its address here, where allocating is allowed
+  // (with lazy module loading the lookup is what places the array on the device). A failure
+  // is left for pyr_dg_rhs_noalloc to retry and report.
+  if (h->equation == PYR_DG_WAVE) {
+    void* p = nullptr;
+    if (noalloc_scratch_address(h->device, &p) != cudaSuccess) cudaGetLastError();
   }
   *out = h;
   return PYR_DG_OK;
@@ -414,10 +583,14 @@ int pyr_dg_project(pyr_dg* h, double t0) {
   if (!std::isfinite(t0)) return fail(PYR_DG_ERR_BAD_ARG, "t0 must be finite");
   DeviceGuard g(h->device);
   CUDA_TRY(g.err);
-  if (h->equation == PYR_DG_ADVECTION)
+  if (h->equation == PYR_DG_ADVECTION) {
     h->L->project1(h->K, h->ev, h->gtab, h->tabd, h->beta, h->box_lo, h->box_hi - h->box_lo, t0, h->q, h->stream);
-  else
+  } else if (h->basis == PYR_DG_NODAL) {  // coefficients into the residual buffer, then nodal values
+    h->L->project(h->K, h->ev, h->gtab, h->tabd, h->bc, t0, h->res, h->stream);
+    nodal_apply(h, nodal_VT(h), h->res, h->q);
+  } else {
     h->L->project(h->K, h->ev, h->gtab, h->tabd, h->bc, t0, h->q, h->stream);
+  }
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemsetAsync(h->res, 0, (size_t)h->K * h->nf * h->Np * h->tsize, h->stream));
   h->t = t0;
@@ -461,6 +634,10 @@ int pyr_dg_rhs(pyr_dg* h, const void* q_dev, void* rhs_dev) {
     h->L->trace1(h->K, q_dev, h->tab, h->tr, h->stream);
     h->L->rhs1(h->K, q_dev, rhs_dev, nullptr, h->tr, h->mapP, h->geo, h->gface, h->invM, h->tab, h->beta, h->tau, 0.0,
                0.0, 0.0, 0, h->stream);
+  } else if (h->basis == PYR_DG_NODAL) {
+    h->L->nodal_trace(h->K, q_dev, h->ntab, h->ntri, h->tr, h->stream);
+    h->L->nodal_rhs(h->K, q_dev, rhs_dev, nullptr, h->tr, h->nmap, h->geo, h->gface, h->invM, h->tab, h->ntab,
+                    h->ntri, h->bc, h->tau, 0.0, 0.0, 0.0, 0, h->stream);
   } else {
     h->L->trace(h->K, q_dev, h->tab, h->tr, h->stream);
     h->L->rhs_out(h->K, q_dev, rhs_dev, h->tr, h->mapP, h->geo, h->gface, h->invM, h->tab, h->bc, h->tau,
@@ -534,6 +711,29 @@ int build_error_cache(pyr_dg* h) {
 }
 }  // namespace
 
+int pyr_dg_l2_diff(pyr_dg* h, const void* qa, const void* qb, double* d2, double* n2) {
+  if (!h || !qa || !qb) return fail(PYR_DG_ERR_BAD_ARG, "null argument");
+  if (h->basis != PYR_DG_MODAL) return fail(PYR_DG_ERR_BAD_ARG, "pyr_dg_l2_diff needs a modal-basis handle");
+  DeviceGuard g(h->device);
+  CUDA_TRY(g.err);
+  const int64_t total = h->K * h->nf * h->Np;
+  if (h->tsize == 8)
+    l2_diff_kernel<double><<<h->err_blocks, 256, 0, h->stream>>>(total, h->nf, h->Np, (const double*)qa,
+                                                                  (const double*)qb, (const double*)h->invM,
+                                                                  h->partial);
+  else
+    l2_diff_kernel<float><<<h->err_blocks, 256, 0, h->stream>>>(total, h->nf, h->Np, (const float*)qa,
+                                                                 (const float*)qb, (const float*)h->invM,
+                                                                 h->partial);
+  CUDA_TRY(cudaGetLastError());
+  double s0 = 0.0, s1 = 0.0;
+  const int rc = read_partial(h, &s0, &s1);
+  if (rc != PYR_DG_OK) return rc;
+  if (d2) *d2 = s0;
+  if (n2) *n2 = s1;
+  return PYR_DG_OK;
+}
+
 int pyr_dg_set_error_cache(pyr_dg* h, int enable) {
   if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
   DeviceGuard g(h->device);
@@ -560,6 +760,14 @@ int pyr_dg_error(pyr_dg* h, double* l2_abs, double* l2_rel) {
     const int rc = read_partial(h, &e2, &n2);
     if (rc != PYR_DG_OK) return rc;
   } else {
+    // the error kernels read semi-nodal coefficients: a nodal state is converted into the trace
+    // buffer (K x Nfc x 4 >= K x 4 x Np doubles), which holds no state between stages in FP64
+    const void* qm = h->q;
+    if (h->basis == PYR_DG_NODAL) {
+      nodal_apply(h, nodal_VinvT(h), h->q, h->tr);
+      CUDA_TRY(cudaGetLastError());
+      qm = h->tr;
+    }
     if (h->ecache_state == 2) {
       const int rc = build_error_cache(h);
       if (rc != PYR_DG_OK) return rc;
@@ -573,7 +781,7 @@ int pyr_dg_error(pyr_dg* h, double* l2_abs, double* l2_rel) {
       const double tp = std::cos(arg), tu = std::sin(arg) * 0.57735026918962576451;
       const double* shat = h->ecache;
       const double* Md = shat + (size_t)h->K * 4 * h->Np;
-      h->L->error_proj(h->K, h->q, shat, Md, tp, tu, h->partial, h->err_blocks, h->stream);
+      h->L->error_proj(h->K, qm, shat, Md, tp, tu, h->partial, h->err_blocks, h->stream);
       CUDA_TRY(cudaGetLastError());
       double zero = 0.0;
       const int rc = read_partial(h, &e2, &zero);
@@ -582,7 +790,7 @@ int pyr_dg_error(pyr_dg* h, double* l2_abs, double* l2_rel) {
       e2 += tp * tp * h->ecache_sum[0] + tu * tu * h->ecache_sum[1];
       n2 = tp * tp * h->ecache_sum[2] + tu * tu * h->ecache_sum[3];
     } else {
-      h->L->error(h->K, h->q, h->ev, h->gtab, h->bc, h->t, h->partial, h->err_blocks, h->stream);
+      h->L->error(h->K, qm, h->ev, h->gtab, h->bc, h->t, h->partial, h->err_blocks, h->stream);
       CUDA_TRY(cudaGetLastError());
       const int rc = read_partial(h, &e2, &n2);
       if (rc != PYR_DG_OK) return rc;
@@ -668,12 +876,29 @@ constexpr int kMaxNoallocDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PYR_DG_NOALLOC_SCRATCH_BYTES];
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kMaxNoallocDevices] = {};
+
+// Host code sees only a stand-in for the array: its device address is fetched once per
+// device, with that device current (the callers hold a DeviceGuard for it).
+cudaError_t noalloc_scratch_address(int device, void** out) {
+  *out = nullptr;
+  if (device < 0 || device >= kMaxNoallocDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[device] = p;
+  }
+  *out = g_noalloc_addr[device];
+  return cudaSuccess;
+}
 }  // namespace
 
 extern "C" int pyr_dg_rhs_noalloc(pyr_dg* h, const void* q_dev, void* rhs_dev) {
   if (!h || !q_dev || !rhs_dev) return fail(PYR_DG_ERR_BAD_ARG, "null argument");
   if (q_dev == rhs_dev) return fail(PYR_DG_ERR_BAD_ARG, "rhs must not alias q");
-  if (h->equation != PYR_DG_WAVE) return fail(PYR_DG_ERR_BAD_ARG, "pyr_dg_rhs_noalloc supports wave handles only");
+  if (h->equation != PYR_DG_WAVE || h->basis != PYR_DG_MODAL)
+    return fail(PYR_DG_ERR_BAD_ARG, "pyr_dg_rhs_noalloc supports modal-basis wave handles only");
   const size_t need = (size_t)h->K * h->Nfc * 4 * h->tsize;
   if (need > (size_t)PYR_DG_NOALLOC_SCRATCH_BYTES)
     return fail(PYR_DG_ERR_BAD_ARG,
@@ -686,17 +911,11 @@ extern "C" int pyr_dg_rhs_noalloc(pyr_dg* h, const void* q_dev, void* rhs_dev) {
   CUDA_TRY(g.err);
   void* scratch = nullptr;
   {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[h->device]) {
-      // host code sees only a stand-in for the array: fetch its device address once per device
-      void* p = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess)
-        return fail(PYR_DG_ERR_CUDA, "cudaGetSymbolAddress(scratch) on device %d: %s", h->device,
-                    cudaGetErrorString(e));
-      g_noalloc_addr[h->device] = p;
-    }
-    scratch = g_noalloc_addr[h->device];
+    // cached by pyr_dg_setup; looked up here only if that failed
+    const cudaError_t e = noalloc_scratch_address(h->device, &scratch);
+    if (e != cudaSuccess)
+      return fail(PYR_DG_ERR_CUDA, "cudaGetSymbolAddress(scratch) on device %d: %s", h->device,
+                  cudaGetErrorString(e));
   }
   h->L->trace(h->K, q_dev, h->tab, scratch, h->stream);
   h->L->rhs_out(h->K, q_dev, rhs_dev, scratch, h->mapP, h->geo, h->gface, h->invM, h->tab, h->bc, h->tau,

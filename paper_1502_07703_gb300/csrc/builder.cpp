@@ -504,4 +504,190 @@ int build_connectivity(const double* V, int64_t Nv, const int32_t* EToV, int64_t
   return 0;
 }
 
+
+// ------------------------------------------------------------ nodal variant
+int gll_points(int n, double* x) {
+  if (n < 1 || n > 64) return -1;
+  if (n == 1) {
+    x[0] = 0.0;
+    return 0;
+  }
+  x[0] = -1.0;
+  x[n - 1] = 1.0;
+  if (n > 2) {  // interior GLL points: the zeros of P'_{n-1}, i.e. of P_{n-2}^{(1,1)}
+    std::vector<double> xi(n - 2), wi(n - 2);
+    gauss_jacobi(n - 2, 1.0, 1.0, xi.data(), wi.data());
+    for (int i = 0; i < n - 2; ++i) x[i + 1] = xi[i];
+  }
+  return 0;
+}
+
+// In-place inverse of the n x n row-major matrix A (Gauss-Jordan, partial pivoting);
+// returns false if a pivot vanishes.
+static bool invert(std::vector<double>& A, int n) {
+  std::vector<double> B((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) B[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = r;
+    if (!(std::fabs(A[(size_t)piv * n + c]) > 1e-300)) return false;
+    if (piv != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(A[(size_t)piv * n + k], A[(size_t)c * n + k]);
+        std::swap(B[(size_t)piv * n + k], B[(size_t)c * n + k]);
+      }
+    const double d = 1.0 / A[(size_t)c * n + c];
+    for (int k = 0; k < n; ++k) {
+      A[(size_t)c * n + k] *= d;
+      B[(size_t)c * n + k] *= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = A[(size_t)r * n + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        A[(size_t)r * n + k] -= f * A[(size_t)c * n + k];
+        B[(size_t)r * n + k] -= f * B[(size_t)c * n + k];
+      }
+    }
+  }
+  A.swap(B);
+  return true;
+}
+
+static double inf_norm(const std::vector<double>& A, int n) {
+  double m = 0.0;
+  for (int r = 0; r < n; ++r) {
+    double s = 0.0;
+    for (int c = 0; c < n; ++c) s += std::fabs(A[(size_t)r * n + c]);
+    m = std::max(m, s);
+  }
+  return m;
+}
+
+int build_nodal(int N, NodalTables& nt) {
+  if (N < 1 || N > 7) return -1;
+  const int n1 = N + 1, Np = num_modes(N), nT = n1 * (n1 + 1) / 2;
+  nt.N = N;
+  nt.Np = Np;
+  nt.nT = nT;
+  std::vector<double> cl(n1);
+  gll_points(n1, cl.data());
+  // nodes: layer m at c = cl[m], the (N+1-m)^2 GLL grid in (a, b); apex layer (0, 0, 1)
+  nt.nodes.clear();
+  std::vector<int> off(n1 + 1, 0);
+  for (int m = 0; m <= N; ++m) {
+    const int nm = n1 - m;
+    std::vector<double> xs(nm);
+    gll_points(nm, xs.data());
+    off[m + 1] = off[m] + nm * nm;
+    for (int q = 0; q < nm; ++q)
+      for (int p = 0; p < nm; ++p) {
+        nt.nodes.push_back(xs[p]);
+        nt.nodes.push_back(xs[q]);
+        nt.nodes.push_back(cl[m]);
+      }
+  }
+  // Vandermonde of the semi-nodal basis phi_(k,j,i) = l_i^k(a) l_j^k(b) G_k(c) at the nodes
+  std::vector<std::vector<double>> xk(n1);
+  for (int k = 0; k <= N; ++k) {
+    std::vector<double> w(k + 1);
+    xk[k].resize(k + 1);
+    gauss_jacobi(k + 1, 0.0, 0.0, xk[k].data(), w.data());
+  }
+  nt.V.assign((size_t)Np * Np, 0.0);
+  std::vector<double> La(n1), Lb(n1), dL(n1);
+  for (int i = 0; i < Np; ++i) {
+    const double a = nt.nodes[3 * i], b = nt.nodes[3 * i + 1], c = nt.nodes[3 * i + 2];
+    for (int k = 0; k <= N; ++k) {
+      double Gk = 0.0;
+      cfun(N, k, c, &Gk, nullptr, nullptr);
+      lagrange(xk[k].data(), k + 1, a, La.data(), dL.data());
+      lagrange(xk[k].data(), k + 1, b, Lb.data(), dL.data());
+      for (int j = 0; j <= k; ++j)
+        for (int ii = 0; ii <= k; ++ii) nt.V[(size_t)i * Np + lvl_off(k) + j * (k + 1) + ii] = La[ii] * Lb[j] * Gk;
+    }
+  }
+  std::vector<double> Vinv = nt.V;
+  if (!invert(Vinv, Np)) return -2;
+  nt.cond_inf = inf_norm(nt.V, Np) * inf_norm(Vinv, Np);
+  nt.VT.assign((size_t)Np * Np, 0.0);
+  nt.VinvT.assign((size_t)Np * Np, 0.0);
+  for (int i = 0; i < Np; ++i)
+    for (int n = 0; n < Np; ++n) {
+      nt.VT[(size_t)n * Np + i] = nt.V[(size_t)i * Np + n];
+      nt.VinvT[(size_t)i * Np + n] = Vinv[(size_t)n * Np + i];
+    }
+  // triangle face: nodes (e, c) per layer (GLL points of the layer's edge), apex last; P_N basis
+  // chi_(al,be)(e, c) = P_al(e) ((1-c)/2)^al P_be^{(2al+1,0)}(c), al + be <= N
+  std::vector<double> te, tc;
+  for (int m = 0; m <= N; ++m) {
+    const int nm = n1 - m;
+    std::vector<double> xs(nm);
+    gll_points(nm, xs.data());
+    for (int t = 0; t < nm; ++t) {
+      te.push_back(nm == 1 ? 0.0 : xs[t]);
+      tc.push_back(cl[m]);
+    }
+  }
+  auto chi = [&](double e, double c, double* out) {
+    int col = 0;
+    for (int al = 0; al <= N; ++al)
+      for (int be = 0; al + be <= N; ++be)
+        out[col++] = jacobi_p(al, 0.0, 0.0, e) * std::pow(0.5 * (1.0 - c), al) * jacobi_p(be, 2.0 * al + 1.0, 0.0, c);
+  };
+  std::vector<double> Vt((size_t)nT * nT);
+  for (int j = 0; j < nT; ++j) chi(te[j], tc[j], &Vt[(size_t)j * nT]);
+  if (!invert(Vt, nT)) return -2;  // Vt now holds the Lagrange coefficients (columns)
+  std::vector<double> xg(n1), wg(n1), xf(n1), wf(n1), row(nT), Lq((size_t)n1 * n1 * nT);
+  gauss_jacobi(n1, 0.0, 0.0, xg.data(), wg.data());
+  gauss_jacobi(n1, 1.0, 0.0, xf.data(), wf.data());
+  std::vector<double> wq((size_t)n1 * n1);
+  for (int mq = 0; mq < n1; ++mq)
+    for (int eq = 0; eq < n1; ++eq) {
+      const int qi = eq + n1 * mq;
+      wq[qi] = wg[eq] * 0.5 * wf[mq];  // collapse factor (1-c)/2 in the Gauss-Jacobi (1,0) weights
+      chi(xg[eq], xf[mq], row.data());
+      for (int j = 0; j < nT; ++j) {
+        double v = 0.0;
+        for (int r = 0; r < nT; ++r) v += row[r] * Vt[(size_t)r * nT + j];
+        Lq[(size_t)qi * nT + j] = v;
+      }
+    }
+  nt.Mtri.assign((size_t)nT * nT, 0.0);
+  for (int qi = 0; qi < n1 * n1; ++qi)
+    for (int i = 0; i < nT; ++i)
+      for (int j = 0; j < nT; ++j)
+        nt.Mtri[(size_t)i * nT + j] += wq[qi] * Lq[(size_t)qi * nT + i] * Lq[(size_t)qi * nT + j];
+  // GLL -> Gauss-Legendre interpolation on the base edge
+  std::vector<double> xl(n1);
+  gll_points(n1, xl.data());
+  nt.I1.assign((size_t)n1 * n1, 0.0);
+  for (int q = 0; q < n1; ++q) {
+    lagrange(xl.data(), n1, xg[q], La.data(), dL.data());
+    for (int p = 0; p < n1; ++p) nt.I1[(size_t)q * n1 + p] = La[p];
+  }
+  // element node of each triangle-face node: face 1 b = -1, 2 a = +1, 3 b = +1, 4 a = -1;
+  // local node (m, t) with t along the face's edge coordinate (a on faces 1 and 3, b on 2 and 4)
+  nt.tri_node.assign((size_t)4 * nT, 0);
+  for (int f = 1; f <= 4; ++f) {
+    int j = 0;
+    for (int m = 0; m <= N; ++m) {
+      const int nm = n1 - m;
+      for (int t = 0; t < nm; ++t, ++j) {
+        int p = 0, q = 0;
+        if (nm > 1) {
+          if (f == 1) { p = t; q = 0; }
+          else if (f == 2) { p = nm - 1; q = t; }
+          else if (f == 3) { p = t; q = nm - 1; }
+          else { p = 0; q = t; }
+        }
+        nt.tri_node[(size_t)(f - 1) * nT + j] = off[m] + q * nm + p;
+      }
+    }
+  }
+  return 0;
+}
+
 }  // namespace pyrdg

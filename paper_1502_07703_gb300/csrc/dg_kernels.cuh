@@ -455,59 +455,18 @@ __device__ __forceinline__ void project_passes(const T* s_tab, const T* Fv, cons
   __syncthreads();
 }
 
-template <int N, typename T, bool UPDATE>
-__global__ void __launch_bounds__(KCfg<N>::NT)
-    rhs_kernel(int64_t K, const T* qin, T* qout, T* __restrict__ res,  // qin == qout when updating in place
-               const T* __restrict__ tr, const int32_t* __restrict__ mapP, const T* __restrict__ geo,
-               const T* __restrict__ gface, const T* __restrict__ invM, const T* __restrict__ tab, int bc, T tau,
-               T rka, T rkb, T dt, const T* __restrict__ dt_elem) {
+// Volume passes of the rhs (a3 with the base-face lift of a5): from the coefficients s_u and
+// the weighted face fluxes s_Fs (written before the call; the first barrier below orders
+// them) to s_Zb, the b^T output the a^T pass reads. Shared by the modal stage kernel and the
+// nodal one; TRI_LIFT = false leaves the triangle-face rows and columns of Y zero (the nodal
+// kernel lifts its triangle faces with face mass matrices instead).
+template <int N, typename T, bool TRI_LIFT>
+__device__ __forceinline__ void volume_passes(const T* s_tab, const T* s_u, const T* s_geo, const T* s_Fs, T* s_A,
+                                              T* s_dA, T* s_U, T* s_Ua, T* s_Ub, T* s_Y, T* s_X, T* s_Zc, T* s_Zb,
+                                              int tid, int nthr) {
   using d = Dims<N>;
-  using S = RhsSmem<N, T>;
   constexpr TabLayout L(N);
-  constexpr int nY = S::nY;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  T* s_tab = sm + S::tab;
-  T* s_u = sm + S::u;
-  T* s_geo = sm + S::geo;
-  T* s_gf = sm + S::gf;
-  T* s_Fs = sm + S::Fs;
-  T* s_A = sm + S::A;
-  T* s_dA = sm + S::dA;
-  T* s_U = sm + S::U;
-  T* s_Ua = sm + S::Ua;
-  T* s_Ub = sm + S::Ub;
-  T* s_Y = sm + S::Y;
-  T* s_X = sm + S::X;
-  T* s_Zc = sm + S::Zc;
-  T* s_Zb = sm + S::Zb;
-  const int64_t e = blockIdx.x;
-  const int tid = threadIdx.x;
-  const int nthr = blockDim.x;
-
-  for (int x = tid; x < L.size; x += nthr) s_tab[x] = tab[x];
-  for (int x = tid; x < 4 * d::Np; x += nthr) s_u[x] = qin[e * 4 * d::Np + x];
-  for (int x = tid; x < d::NGEO * d::n2; x += nthr) s_geo[x] = geo[e * d::NGEO * d::n2 + x];
-  for (int x = tid; x < d::NGF; x += nthr) s_gf[x] = gface[e * d::NGF + x];
-  __syncthreads();
-
-  // surface flux at every face point (a4), weighted by w sJ
-  for (int g = tid; g < d::Nfc; g += nthr) {
-    const int face = g / d::n2, idx = g % d::n2;
-    const int64_t gl = e * d::Nfc + g;
-    const int64_t gn = mapP[gl];
-    T um[4], up[4], F[4];
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      um[f] = tr[gl * 4 + f];
-      up[f] = tr[gn * 4 + f];
-    }
-    const T* nv = face == 0 ? s_gf + 16 + 4 * idx : s_gf + 4 * (face - 1);
-    const T w = face == 0 ? s_tab[L.WB + idx] : s_tab[L.WFT + idx];
-    face_flux<T>(um, up, gn == gl, bc, tau, nv, w * nv[3], F);
-#pragma unroll
-    for (int f = 0; f < 4; ++f) s_Fs[f * d::Nfc + g] = F[f];
-  }
+  constexpr int nY = d::P3 * d::P3;
   // a pass, level-major: A = l^k(a_p) u, dA = l^k'(a_p) u. Levels run in the order
   // 1..N-1, 0, N: the warp that straddles into level N's short form then also holds
   // the cheapest level.
@@ -634,8 +593,10 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
       const T* fs = s_Fs + f * d::Nfc + face * d::n2 + ee;
       const T* gfk = s_tab + L.GF + k * d::n1;
       T acc = 0;
+      if (TRI_LIFT) {
 #pragma unroll
-      for (int m = 0; m <= N; ++m) acc += gfk[m] * fs[m * d::n1];
+        for (int m = 0; m <= N; ++m) acc += gfk[m] * fs[m * d::n1];
+      }
       T* Yk = s_Y + (f * d::n1 + k) * nY;
       if (slot < 2)
         Yk[ee * d::P3 + d::n1 + slot] = acc;  // b = -1, +1 columns
@@ -675,6 +636,61 @@ __global__ void __launch_bounds__(KCfg<N>::NT)
     s_Zb[(f * d::nrow + row) * d::P3 + pp] = acc;
   }
   __syncthreads();
+}
+
+template <int N, typename T, bool UPDATE>
+__global__ void __launch_bounds__(KCfg<N>::NT)
+    rhs_kernel(int64_t K, const T* qin, T* qout, T* __restrict__ res,  // qin == qout when updating in place
+               const T* __restrict__ tr, const int32_t* __restrict__ mapP, const T* __restrict__ geo,
+               const T* __restrict__ gface, const T* __restrict__ invM, const T* __restrict__ tab, int bc, T tau,
+               T rka, T rkb, T dt, const T* __restrict__ dt_elem) {
+  using d = Dims<N>;
+  using S = RhsSmem<N, T>;
+  constexpr TabLayout L(N);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* s_tab = sm + S::tab;
+  T* s_u = sm + S::u;
+  T* s_geo = sm + S::geo;
+  T* s_gf = sm + S::gf;
+  T* s_Fs = sm + S::Fs;
+  T* s_A = sm + S::A;
+  T* s_dA = sm + S::dA;
+  T* s_U = sm + S::U;
+  T* s_Ua = sm + S::Ua;
+  T* s_Ub = sm + S::Ub;
+  T* s_Y = sm + S::Y;
+  T* s_X = sm + S::X;
+  T* s_Zc = sm + S::Zc;
+  T* s_Zb = sm + S::Zb;
+  const int64_t e = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int nthr = blockDim.x;
+
+  for (int x = tid; x < L.size; x += nthr) s_tab[x] = tab[x];
+  for (int x = tid; x < 4 * d::Np; x += nthr) s_u[x] = qin[e * 4 * d::Np + x];
+  for (int x = tid; x < d::NGEO * d::n2; x += nthr) s_geo[x] = geo[e * d::NGEO * d::n2 + x];
+  for (int x = tid; x < d::NGF; x += nthr) s_gf[x] = gface[e * d::NGF + x];
+  __syncthreads();
+
+  // surface flux at every face point (a4), weighted by w sJ
+  for (int g = tid; g < d::Nfc; g += nthr) {
+    const int face = g / d::n2, idx = g % d::n2;
+    const int64_t gl = e * d::Nfc + g;
+    const int64_t gn = mapP[gl];
+    T um[4], up[4], F[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      um[f] = tr[gl * 4 + f];
+      up[f] = tr[gn * 4 + f];
+    }
+    const T* nv = face == 0 ? s_gf + 16 + 4 * idx : s_gf + 4 * (face - 1);
+    const T w = face == 0 ? s_tab[L.WB + idx] : s_tab[L.WFT + idx];
+    face_flux<T>(um, up, gn == gl, bc, tau, nv, w * nv[3], F);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) s_Fs[f * d::Nfc + g] = F[f];
+  }
+  volume_passes<N, T, true>(s_tab, s_u, s_geo, s_Fs, s_A, s_dA, s_U, s_Ua, s_Ub, s_Y, s_X, s_Zc, s_Zb, tid, nthr);
   // a^T pass, M^{-1} (a6), LSRK stage (a7). Items run level-major (k, f, j, i) so that
   // a warp's lanes share a level: level N takes the short form below.
   for (int y = tid; y < 4 * d::Np; y += nthr) {

@@ -50,6 +50,14 @@ struct pyr_dg {
   double* ecache = nullptr;
   double ecache_sum[4] = {0.0, 0.0, 0.0, 0.0};
   int ecache_mode = 1, ecache_state = 0;
+  // nodal variant (basis == PYR_DG_NODAL): per-degree table (V, V^T, V^{-T}, triangle nodal
+  // mass, GLL -> GL interpolation), element nodes of the triangle faces (4 x nT), and the
+  // matching trace point of every trace point (K x ntr; itself on a boundary)
+  int basis = 0;
+  int ntr = 0;
+  double* ntab = nullptr;
+  int32_t* ntri = nullptr;
+  int32_t* nmap = nullptr;
   // per-kernel event timing of pyr_dg_step (pyr_dg_profile)
   bool profiling = false;
   std::vector<cudaEvent_t> events;

@@ -5,6 +5,7 @@
 #include "adv32.cuh"
 #include "adv_kernels.cuh"
 #include "launch.h"
+#include "nodal.cuh"
 
 namespace pyrdg {
 
@@ -50,6 +51,15 @@ struct Impl {
     e = cudaFuncSetAttribute(exact_proj_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)ProjQSmem<N>::bytes);
     if (e != cudaSuccess) return e;
+    if constexpr (sizeof(T) == 8) {
+      static_assert(NodalSmem<N>::bytes <= kMaxSmem, "nodal stage kernel shared memory");
+      e = cudaFuncSetAttribute(nodal_rhs_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)NodalSmem<N>::bytes);
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(nodal_rhs_kernel<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)NodalSmem<N>::bytes);
+      if (e != cudaSuccess) return e;
+    }
     return cudaFuncSetAttribute(error_kernel<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)ErrSmem<N>::bytes);
   }
@@ -122,6 +132,29 @@ struct Impl {
   static void error_proj(int64_t K, const void* q, const double* shat, const double* Mdiag, double tp, double tu,
                          double* partial, int nblocks, cudaStream_t s) {
     error_proj_kernel<N, T><<<nblocks, 256, 0, s>>>(K, (const T*)q, shat, Mdiag, tp, tu, partial);
+  }
+  static void nodal_trace(int64_t K, const void* q, const double* ntab, const int32_t* tri_node, void* tr,
+                          cudaStream_t s) {
+    if constexpr (sizeof(T) == 8) {
+      const int64_t total = K * NodalDims<N>::NTR;
+      const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+      nodal_trace_kernel<N><<<blocks, 256, 0, s>>>(K, (const double*)q, ntab, tri_node, (double*)tr);
+    }
+  }
+  static void nodal_rhs(int64_t K, const void* qin, void* qout, void* res, const void* tr, const int32_t* nmap,
+                        const void* geo, const void* gface, const void* invM, const void* tab, const double* ntab,
+                        const int32_t* tri_node, int bc, double tau, double rka, double rkb, double dt, int update,
+                        cudaStream_t s) {
+    if constexpr (sizeof(T) == 8) {
+      if (update)
+        nodal_rhs_kernel<N, true><<<(unsigned)K, NT, NodalSmem<N>::bytes, s>>>(
+            K, (const double*)qin, (double*)qout, (double*)res, (const double*)tr, nmap, (const double*)geo,
+            (const double*)gface, (const double*)invM, (const double*)tab, ntab, tri_node, bc, tau, rka, rkb, dt);
+      else
+        nodal_rhs_kernel<N, false><<<(unsigned)K, NT, NodalSmem<N>::bytes, s>>>(
+            K, (const double*)qin, (double*)qout, nullptr, (const double*)tr, nmap, (const double*)geo,
+            (const double*)gface, (const double*)invM, (const double*)tab, ntab, tri_node, bc, tau, 0.0, 0.0, 0.0);
+    }
   }
   template <int E>
   static void stage32_e(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
@@ -279,6 +312,10 @@ struct Impl {
     l.rhs1 = &rhs1;
     l.project1 = &project1;
     l.error1 = &error1;
+    l.nodal_ntr = NodalDims<N>::NTR;
+    l.nodal_ntab = NodalDims<N>::size;
+    l.nodal_trace = sizeof(T) == 8 ? &nodal_trace : nullptr;
+    l.nodal_rhs = sizeof(T) == 8 ? &nodal_rhs : nullptr;
     if (sizeof(T) == 4) {
       l.stage32 = &stage32;
       l.upload_c32 = &upload_c32;

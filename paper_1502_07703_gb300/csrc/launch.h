@@ -62,6 +62,18 @@ struct Launchers {
                    double lo, double L, double t, void* q, cudaStream_t s);
   void (*error1)(int64_t K, const void* q, const double* ev, const double* gtab, const double* beta, double lo,
                  double L, double t, double* partial, int nblocks, cudaStream_t s);
+  // Nodal variant (Sec. 4.4.1; double only, null for float): the trace points of a nodal
+  // state (base Gauss-Legendre points, triangle-face nodes) and the stage / rhs from them.
+  // ntab: NodalDims<N> table; tri_node: 4 x nT element nodes of the triangle faces; nmap:
+  // K x NTR matching trace point (itself on a boundary).
+  void (*nodal_trace)(int64_t K, const void* q, const double* ntab, const int32_t* tri_node, void* tr,
+                      cudaStream_t s);
+  void (*nodal_rhs)(int64_t K, const void* qin, void* qout, void* res, const void* tr, const int32_t* nmap,
+                    const void* geo, const void* gface, const void* invM, const void* tab, const double* ntab,
+                    const int32_t* tri_node, int bc, double tau, double rka, double rkb, double dt, int update,
+                    cudaStream_t s);
+  int nodal_ntr;      // trace points per element of the nodal variant
+  int nodal_ntab;     // doubles in its table
 };
 
 // precision: 0 = double, 1 = float. Returns null for an unsupported degree.
