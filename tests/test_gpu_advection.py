@@ -4,13 +4,13 @@ CUDA path against the FP64 oracle (oracle/advection.py)."""
 import numpy as np
 import pytest
 
+from _parity import TOL, check
 from oracle.advection import PyramidAdvection
 from paper_1502_07703_gb300.mesh import make_pyramid_mesh, random_state
 
 pytestmark = pytest.mark.gpu
 
 BETA = (1.0, 0.3, -0.2)
-TOL = {"f64": 1e-12, "f32": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -41,8 +41,7 @@ def test_advection_rhs_parity(torch_cuda, N, precision):
             R = s.rhs(torch.tensor(U, dtype=s.torch_dtype, device="cuda")).double().cpu().numpy()
         Uin = U.astype(np.float32).astype(np.float64) if precision == "f32" else U
         Ro = ad.rhs(ad.dg.psi_from_phi(Uin))
-        rel = ad.dg.rel_l2_points(ad.dg.values_phi(R), ad.dg.values_psi(Ro))
-        assert rel <= TOL[precision], (alpha, rel)
+        check(ad.dg, ad.dg.values_phi(R), ad.dg.values_psi(Ro), TOL[precision], alpha)
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
@@ -60,10 +59,8 @@ def test_advection_evolution_projection_and_error(torch_cuda, precision):
         s.step(10, dt)
         G = s.get_state().astype(np.float64)
         err = s.error()
-    rel0 = ad.dg.rel_l2_points(ad.dg.values_phi(P), ad.dg.values_psi(U0))
-    rel = ad.dg.rel_l2_points(ad.dg.values_phi(G), ad.dg.values_psi(U10))
-    assert rel0 <= (1e-13 if precision == "f64" else 1e-6), rel0
-    assert rel <= TOL[precision], rel
+    check(ad.dg, ad.dg.values_phi(P), ad.dg.values_psi(U0), 1e-13 if precision == "f64" else 1e-6, "projection")
+    check(ad.dg, ad.dg.values_phi(G), ad.dg.values_psi(U10), TOL[precision], "10 steps")
     eo = ad.error(U10, 10 * dt)
     np.testing.assert_allclose(err, eo, rtol=1e-9 if precision == "f64" else 1e-3)
 
@@ -85,5 +82,4 @@ def test_advection_f32_stage_kernel_all_degrees(torch_cuda, N):
         s.step(2, dt)
         s.step(3, dt)
         G = s.get_state().astype(np.float64)
-    rel = ad.dg.rel_l2_points(ad.dg.values_phi(G), ad.dg.values_psi(U6))
-    assert rel <= TOL["f32"], rel
+    check(ad.dg, ad.dg.values_phi(G), ad.dg.values_psi(U6), TOL["f32"])

@@ -65,3 +65,26 @@ def test_noalloc_rejects_mesh_beyond_static_scratch(torch_cuda):
         rc = binding.lib().pyr_dg_rhs_noalloc(s._h, q.data_ptr(), out.data_ptr())
         assert rc == -1
         assert b"static scratch holds" in binding.lib().pyr_dg_last_error()
+
+
+def test_noalloc_takes_no_device_memory_and_ignores_stale_scratch(torch_cuda):
+    """A caller that cannot allocate sees free device memory unchanged across the call, and a
+    call after a larger mesh's call (whose traces are still in the array) is unaffected by them."""
+    torch = torch_cuda
+    from paper_1502_07703_gb300.binding import Solver
+    vb, eb = make_pyramid_mesh(4, 4, 3, delta=0.08, seed=22)  # 288 pyramids: 1.7 MB of traces at N = 5
+    vs, es = make_pyramid_mesh(2, 1, 1, delta=0.08, seed=23)  # 12 pyramids
+    with Solver(vb, eb, 5) as big, Solver(vs, es, 5) as small:
+        qb = torch.tensor(random_state(big.K, big.Np, 41), dtype=big.torch_dtype, device="cuda")
+        qs = torch.tensor(random_state(small.K, small.Np, 42), dtype=small.torch_dtype, device="cuda")
+        ref_s = small.rhs(qs)
+        ob, os_ = torch.empty_like(qb), torch.empty_like(qs)
+        _noalloc(big, qb, ob)  # warm: both handles' kernels are loaded
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        _noalloc(big, qb, ob)
+        _noalloc(small, qs, os_)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        a, b = os_.cpu().numpy(), ref_s.cpu().numpy()
+        assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b)
