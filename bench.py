@@ -195,19 +195,40 @@ def max_over_ranks(x, world, device):
     return float(t.item())
 
 
+def measured_traffic(kernel, K):
+    """DRAM bytes per launch of `kernel` at K elements from the ncu capture recorded in
+    profiles/dram_traffic.json (bytes per element, scaled by K), or (None, reason) when no
+    capture is recorded or the kernel's sources changed since it was taken (their SHA-256
+    is stored with the figure)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as fh:
+            rec = json.load(fh)[kernel]
+    except (OSError, ValueError, KeyError):
+        return None, "no ncu capture recorded for this kernel"
+    h = hashlib.sha256()
+    for src in rec["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != rec["sha256"]:
+        return None, "kernel sources changed since the recorded ncu capture"
+    return rec["bytes_per_element"] * K, rec["capture"]
+
+
 def whole_job_rate(units_per_rank, seconds_max, world):
     """Whole-job throughput of independent replicas: every rank processed units_per_rank
     units; the job took the slowest rank's time (weak scaling, no data-path collective)."""
     return world * units_per_rank / seconds_max
 
 
-def oracle_sample(steps, warmup):
-    """The CPU oracle (plain FP64 numpy, dense matrices) on the 8^3-hex sample."""
+def oracle_sample(steps, warmup, threads=1):
+    """The CPU oracle (plain FP64 numpy, dense matrices) on the 8^3-hex sample, its
+    per-element contractions on `threads` host threads (element chunks)."""
     from oracle.dg import PyramidDG
     from paper_1502_07703_gb300.mesh import make_pyramid_mesh
 
     v, e = make_pyramid_mesh(SAMPLE_NX, delta=DELTA, seed=SEED)
-    dg = PyramidDG(v, e, N)
+    dg = PyramidDG(v, e, N, threads=threads)
     U = dg.project_exact(0.0)
     dt = dg.dt_cfl(0.5)
     for _ in range(warmup):
@@ -217,16 +238,27 @@ def oracle_sample(steps, warmup):
         U = dg.lsrk4(U, dt, 1)
     el = time.perf_counter() - t0
     dofs = dg.K * dg.Np * 4 * 5 * steps
-    return {"value": dofs / el, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+    how = "one thread" if threads == 1 else f"{threads} threads over element chunks"
+    return {"value": dofs / el, "unit": "DOF-updates/s", "cores": threads, "kind": "oracle",
+            "host_cpu_count": os.cpu_count(),
             "sample": f"{SAMPLE_NX}^3 hexes x 6 = {dg.K} pyramids, N={N}, {steps} LSRK4 step(s) = {5 * steps} "
-                      f"RK stages, {el:.1f} s; numpy einsum on one thread"}, el
+                      f"RK stages, {el:.1f} s; numpy einsum on {how}"}, el
+
+
+def cpu_baseline_all_and_one(steps_all, steps_one):
+    """The oracle on all host cores (the reported baseline) and on one core."""
+    cores = os.cpu_count() or 1
+    allc, _ = oracle_sample(steps_all, 1, threads=cores)
+    one, _ = oracle_sample(steps_one, 1, threads=1)
+    allc["one_core"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
+    return allc
 
 
 def run_reference(args, world, rank):
     """Reference arm: the oracle timed on the host cores (rank 0 only)."""
     if rank != 0:
         return
-    base, el = oracle_sample(args.steps, args.warmup)
+    base, el = oracle_sample(args.steps, args.warmup, threads=os.cpu_count() or 1)
     line = {
         "impl": "reference", "metric": METRIC, "value": base["value"], "unit": "DOF-updates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
@@ -281,7 +313,57 @@ def measure_form(binding, nx, delta, seed, n, precision, steps, warmup, dev):
                                         stage_bytes_per_element(n, 4), "achieved_gbs": gbs,
                                         "hbm_peak_gbs": HBM_GBS, "hbm_peak_kind": HBM_KIND,
                                         "hbm_frac": gbs / HBM_GBS}
+        # error of the FP32 path as a number: 10 steps from the projected standing wave against
+        # the same 10 steps of the FP64 path (which matches the FP64 oracle to <= 1e-12 in the
+        # parity tests), as the L2 norm of the difference over the L2 norm of the FP64 state
+        cmp_steps = 10
+        s.project(0.0)
+        s.step(cmp_steps, dt)
+        q32 = s.get_state(device=True).double()
+        s.close()
+        with binding.Solver(v, e, n, precision="f64", bc="wall", tau=1.0, device=dev) as s64:
+            s64.project(0.0)
+            s64.step(cmp_steps, dt)
+            d, nb = s64.l2_diff(q32, s64.get_state(device=True))
+        out["rel_l2_vs_f64_gpu"] = {"value": d / nb, "steps": cmp_steps,
+                                    "norm": "L2 over the mesh (diagonal mass matrix, pyr_dg_l2_diff)"}
+        return out
     s.close()
+    return out
+
+
+def measure_nodal_vs_modal(binding, nx, n, steps, warmup, dev):
+    """FP64 stage times of the nodal variant (Sec. 4.4.1: nodal state, M^{-1} through the change
+    of basis, nodal face mass matrices on the triangle faces) beside the modal path, same mesh
+    (nx^3 hexes x 6, +-0.05h, seed 1), degree n and step."""
+    import torch
+    from paper_1502_07703_gb300.mesh import make_pyramid_mesh
+
+    v, e = make_pyramid_mesh(nx, delta=DELTA, seed=SEED)
+    out = {"mesh": f"{nx}^3 hexes x 6, +-{DELTA}h (seed {SEED})", "K": 6 * nx ** 3, "N": n, "precision": "f64",
+           "steps": steps}
+    for basis in ("modal", "nodal"):
+        s = binding.Solver(v, e, n, precision="f64", bc="wall", tau=1.0, device=dev, basis=basis)
+        dt = s.dt_cfl(0.5)
+        s.project(0.0)
+        for _ in range(warmup):
+            s.step(1, dt)
+        s.sync()
+        s.profile(True)
+        stream = torch.cuda.current_stream(dev)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s.step(steps, dt)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        prof = s.profile_read()
+        s.profile(False)
+        out[basis] = {"ms_per_step": ev0.elapsed_time(ev1) / steps,
+                      "stage_kernel_ms": prof["rhs"][0] / prof["rhs"][1],
+                      "trace_kernel_ms": prof["trace"][0] / prof["trace"][1],
+                      "l2_rel_error_vs_exact": s.error()[1]}
+        s.close()
+    out["nodal_over_modal_step_time"] = out["nodal"]["ms_per_step"] / out["modal"]["ms_per_step"]
     return out
 
 
@@ -366,7 +448,10 @@ def measure_batch(binding, steps, warmup, dev, count=256):
     return out
 
 
-def matched_accuracy(binding, dev, T=0.005):
+MATCHED_CASES = ((8, 2), (16, 2), (32, 2), (8, 3), (16, 3), (32, 3), (8, 4), (16, 4), (32, 4), (16, 5), (32, 5))
+
+
+def matched_accuracy(binding, dev, T=0.005, cases=MATCHED_CASES):
     """FP32 against FP64 at matched L2 error against the exact solution.
 
     Both precisions run the same (mesh, N) cases to the same final time T from
@@ -380,7 +465,7 @@ def matched_accuracy(binding, dev, T=0.005):
     from paper_1502_07703_gb300.mesh import make_pyramid_mesh
 
     rows = []
-    for nx, n in ((8, 2), (16, 2), (32, 2), (8, 3), (16, 3), (32, 3), (8, 4), (16, 4), (32, 4), (16, 5), (32, 5)):
+    for nx, n in cases:
         v, e = make_pyramid_mesh(nx, delta=DELTA, seed=SEED)
         for prec in ("f64", "f32"):
             s = binding.Solver(v, e, n, precision=prec, device=dev)
@@ -401,7 +486,14 @@ def matched_accuracy(binding, dev, T=0.005):
             rows.append({"nx": nx, "N": n, "K": s.K, "precision": prec, "steps": steps, "l2_rel_error": err,
                          "ms_per_unit_time": ms / T, "ms_total": ms})
             s.close()
-    return {"T": T, "rows": rows}
+    pairs = []
+    for i in range(0, len(rows), 2):
+        r64, r32 = rows[i], rows[i + 1]
+        matched = abs(r32["l2_rel_error"] - r64["l2_rel_error"]) <= 0.2 * r64["l2_rel_error"]
+        pairs.append({"nx": r64["nx"], "N": r64["N"], "f64_error": r64["l2_rel_error"],
+                      "f32_error": r32["l2_rel_error"], "errors_within_20pct": matched,
+                      "f32_speedup": r64["ms_total"] / r32["ms_total"]})
+    return {"T": T, "rows": rows, "pairs": pairs}
 
 
 def main():
@@ -495,13 +587,10 @@ def main():
     # the FP32 stage kernel also interpolates the new state to the face points
     flops_el = rhs_flops_per_element(nd) + (trace_flops_per_element(nd) if prec == "f32" else 0)
     achieved = flops_el * K / rhs_avg_s / 1e12
-    # DRAM bytes per element of the FP64 fused stage kernel, from the ncu capture summarised
-    # in profiles/rhs_kernel_n4_f64_24cube.md (82,944 pyramids, N = 4: 1195.2 MB read +
-    # write per launch), scaled by the element count. Valid for that kernel version only:
-    # set to None when the kernel changes, until it is measured again.
-    traffic = 14410.0 * K if (nd == 4 and prec == "f64" and args.nx >= 24) else None
+    kname = f"rhs_kernel<{nd},double,update>" if prec == "f64" else f"stage32_kernel<{nd}>"
+    traffic, traffic_src = measured_traffic(kname, K)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": f"rhs_kernel<{nd},double,update>" if prec == "f64" else f"stage32_kernel<{nd}>",
+                "traffic": traffic, "traffic_source": traffic_src, "kernel": kname,
                 "peak_kind": f"{prec.upper()} FMA throughput measured in this run",
                 "kernel_ms_avg": rhs_ms / rhs_n, "trace_kernel_ms_avg": tr_ms / tr_n if tr_n else 0.0,
                 "kernel_share": rhs_ms / (rhs_ms + tr_ms)}
@@ -539,12 +628,17 @@ def main():
                                                          (64, 0.1, 3, 5, "f32", 10)):
             forms.append(measure_form(binding, f_nx, f_delta, f_seed, f_n, f_prec, f_st, 2, dev))
         forms.append(measure_batch(binding, 10, 2, dev))
+        for n_nodal in (3, 4, 5):
+            forms.append(measure_nodal_vs_modal(binding, NX, n_nodal, 3, 1, dev))
         forms.append(measure_advection(binding, NX, 4, "f64", 10, 2, dev))
         forms.append(measure_advection(binding, NX, 4, "f32", 20, 2, dev))
 
+    matched = None
+    if not args.no_forms:
+        matched = matched_accuracy(binding, dev, cases=((16, 2), (8, 3)))
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu, _ = oracle_sample(15, 1)
+        cpu = cpu_baseline_all_and_one(20, 12)
     line = {
         "metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -561,6 +655,7 @@ def main():
         "cpu_baseline": cpu,
         "l2_error_vs_exact": {"abs": err_abs, "rel": err_rel},
         "precision_forms": forms,
+        "matched_accuracy": matched,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
