@@ -2,10 +2,15 @@
 // together. Meshes of the same degree are stored as one disjoint-union mesh (no
 // face is shared across meshes), so each RK stage is one persistent launch per
 // degree over all of them; each element carries its own mesh's time step. A
-// whole batch step is captured once as a CUDA graph and replayed. For FP32
-// batches the elements per CTA and the persistent grid of each degree are
-// autotuned at setup by timing candidates on the (all-zero) initial state, which
-// leaves it unchanged.
+// whole batch step is captured once as a CUDA graph and replayed; the degree
+// groups are independent, so the graph forks them onto parallel branches (one
+// stream each) and their launches of a stage run side by side, the tail of one
+// overlapping the others. FP32 groups keep their face traces in a ping-pong pair
+// across replays: a step flips the current half 5 x nsteps times, so two graphs
+// (one per starting half) alternate and no replay re-interpolates the traces.
+// For FP32 batches the elements per CTA and the persistent grid of each degree
+// are autotuned at setup by timing candidates on the (all-zero) initial state,
+// which leaves it unchanged.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,16 +41,21 @@ struct pyr_dg_batch {
   std::vector<double> mesh_t;       // simulation time of each mesh
   std::vector<double> mesh_aov;     // max |dK|/|K| of each mesh
   std::vector<double> last_dt;      // per-mesh steps currently in the groups' dt_elem
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by the trace half the replay starts from
   int graph_nsteps = -1;
+  std::vector<cudaStream_t> branch;  // one stream per degree group after the first (graph branches)
+  std::vector<cudaEvent_t> branch_ev;  // fork event, then one join event per branch
 };
 
 namespace {
 
 void destroy_batch(pyr_dg_batch* b) {
   if (!b) return;
-  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (cudaGraphExec_t& g : b->graph)
+    if (g) cudaGraphExecDestroy(g);
   for (pyr_dg* h : b->groups) pyr_dg_destroy(h);
+  for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->branch_ev) cudaEventDestroy(ev);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -89,6 +99,7 @@ int pyr_dg_batch_setup(int nmesh, const double* const* vertices, const int64_t* 
   pyr_dg_default_opts(&o);
   if (opts) o = *opts;
   if (o.equation != PYR_DG_WAVE) return fail(PYR_DG_ERR_BAD_ARG, "batches hold acoustic-wave meshes only");
+  if (o.basis != PYR_DG_MODAL) return fail(PYR_DG_ERR_BAD_ARG, "batches use the modal basis");
   for (int i = 0; i < nmesh; ++i) {
     if (!vertices[i] || !EToV[i] || Nv[i] < 5 || K[i] < 1)
       return fail(PYR_DG_ERR_BAD_ARG, "mesh %d: null arrays or empty sizes", i);
@@ -213,6 +224,23 @@ int pyr_dg_batch_setup(int nmesh, const double* const* vertices, const int64_t* 
       h->tr_valid = false;
     }
   }
+  // graph branches: a stream per further degree group, a fork event and a join event per branch
+  for (size_t g = 1; g < b->groups.size(); ++g) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      destroy_batch(b);
+      return fail(PYR_DG_ERR_CUDA, "cannot create a branch stream");
+    }
+    b->branch.push_back(st);
+  }
+  for (size_t g = 0; g < b->groups.size(); ++g) {
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      destroy_batch(b);
+      return fail(PYR_DG_ERR_CUDA, "cannot create a branch event");
+    }
+    b->branch_ev.push_back(ev);
+  }
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
     destroy_batch(b);
     return fail(PYR_DG_ERR_CUDA, "batch setup failed");
@@ -299,31 +327,64 @@ int pyr_dg_batch_step(pyr_dg_batch* b, int nsteps, const double* dt) {
     }
     b->last_dt.assign(dt, dt + b->nmesh);
   }
-  if (!b->graph || b->graph_nsteps != nsteps) {
-    if (b->graph) {
-      cudaGraphExecDestroy(b->graph);
-      b->graph = nullptr;
+  if (b->graph_nsteps != nsteps) {
+    for (cudaGraphExec_t& gx : b->graph)
+      if (gx) {
+        cudaGraphExecDestroy(gx);
+        gx = nullptr;
+      }
+    b->graph_nsteps = nsteps;
+  }
+  // FP32 groups: traces of the current state in half 0 of the ping-pong pair when any group's
+  // are stale (after setup, projection or a state change); all groups then share the half
+  bool stale = false;
+  for (pyr_dg* h : b->groups) stale = stale || (h->use_stage32 && !h->tr_valid);
+  if (stale) {
+    for (pyr_dg* h : b->groups) {
+      if (!h->use_stage32) continue;
+      h->tr_cur = 0;
+      h->L->trace(h->K, h->q, h->tab, h->tr, b->stream);
+      h->tr_valid = true;
     }
+    CUDA_TRY(cudaGetLastError());
+  }
+  int par = 0;
+  for (pyr_dg* h : b->groups)
+    if (h->use_stage32) par = h->tr_cur;
+  if (!b->graph[par]) {
+    // group 0 on the batch stream, group g > 0 on branch g-1, forked from and joined into it
     cudaGraph_t graph = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     int rc = PYR_DG_OK;
-    for (pyr_dg* h : b->groups) {
-      h->tr_valid = false;  // every replay starts from the traces of the current state
-      if (rc == PYR_DG_OK) rc = pyrdg::enqueue_steps(h, nsteps, 1.0);
+    cudaError_t ce = cudaEventRecord(b->branch_ev[0], b->stream);
+    for (size_t g = 1; g < b->groups.size() && ce == cudaSuccess; ++g)
+      ce = cudaStreamWaitEvent(b->branch[g - 1], b->branch_ev[0], 0);
+    for (size_t g = 0; g < b->groups.size() && ce == cudaSuccess && rc == PYR_DG_OK; ++g) {
+      pyr_dg* h = b->groups[g];
+      const cudaStream_t own = h->stream;
+      h->stream = g == 0 ? b->stream : b->branch[g - 1];
+      rc = pyrdg::enqueue_steps(h, nsteps, 1.0);  // flips tr_cur on the host: restored below
+      h->stream = own;
+      h->tr_cur = par;
+      h->tr_valid = true;
     }
-    const cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
-    if (rc != PYR_DG_OK) {
+    for (size_t g = 1; g < b->groups.size() && ce == cudaSuccess; ++g) {
+      ce = cudaEventRecord(b->branch_ev[g], b->branch[g - 1]);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->stream, b->branch_ev[g], 0);
+    }
+    const cudaError_t ee = cudaStreamEndCapture(b->stream, &graph);
+    if (rc != PYR_DG_OK || ce != cudaSuccess || ee != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
-      return rc;
+      if (rc != PYR_DG_OK) return rc;
+      return fail(PYR_DG_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ee));
     }
-    if (ce != cudaSuccess) return fail(PYR_DG_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
-    const cudaError_t ie = cudaGraphInstantiate(&b->graph, graph, 0);
+    const cudaError_t ie = cudaGraphInstantiate(&b->graph[par], graph, 0);
     cudaGraphDestroy(graph);
     if (ie != cudaSuccess) return fail(PYR_DG_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ie));
-    b->graph_nsteps = nsteps;
   }
-  CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
-  for (pyr_dg* h : b->groups) h->tr_valid = false;
+  CUDA_TRY(cudaGraphLaunch(b->graph[par], b->stream));
+  for (pyr_dg* h : b->groups)
+    if (h->use_stage32) h->tr_cur = (h->tr_cur + 5 * nsteps) & 1;  // the half the replay ended in
   for (int i = 0; i < b->nmesh; ++i) b->mesh_t[i] += nsteps * dt[i];
   return PYR_DG_OK;
 }

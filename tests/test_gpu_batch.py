@@ -8,6 +8,7 @@ against the FP64 oracle."""
 import numpy as np
 import pytest
 
+from _parity import check
 from oracle.dg import PyramidDG
 from paper_1502_07703_gb300.mesh import make_pyramid_mesh
 
@@ -66,8 +67,7 @@ def test_batch_matches_single_mesh_runs_and_oracle(torch_cuda, precision, tol_si
             dg = PyramidDG(v, e, n)
             # the 2N-storage residual restarts at every step (A_1 = 0), so steps compose
             Ur = dg.lsrk4(dg.lsrk4(dg.project_exact(0.0), dt[i], 6), dt2[i], 2)
-            r = dg.rel_l2_points(dg.values_phi(states[i]), dg.values_psi(Ur))
-            assert r <= tol_oracle, (i, r)
+            check(dg, dg.values_phi(states[i]), dg.values_psi(Ur), tol_oracle, i)
 
 
 def test_batch_autotuned_elements_per_block(torch_cuda):
@@ -114,8 +114,7 @@ def test_batch_lowest_and_highest_degrees(torch_cuda, precision, tol):
     for i, (v, e, n) in enumerate(meshes):
         dg = PyramidDG(v, e, n)
         Ur = dg.lsrk4(dg.project_exact(0.0), dt[i], 3)
-        r = dg.rel_l2_points(dg.values_phi(states[i]), dg.values_psi(Ur))
-        assert r <= tol, (n, r)
+        check(dg, dg.values_phi(states[i]), dg.values_psi(Ur), tol, n)
 
 
 def test_batch_oracle_parity_fixed_dt(torch_cuda):
@@ -130,8 +129,7 @@ def test_batch_oracle_parity_fixed_dt(torch_cuda):
     for i, (v, e, n) in enumerate(meshes):
         dg = PyramidDG(v, e, n)
         Ur = dg.lsrk4(dg.project_exact(0.0), dt[i], 4)
-        r = dg.rel_l2_points(dg.values_phi(states[i]), dg.values_psi(Ur))
-        assert r <= 1e-12, (i, r)
+        check(dg, dg.values_phi(states[i]), dg.values_psi(Ur), 1e-12, i)
 
 
 def test_batch_rejects_bad_input(torch_cuda):
@@ -142,3 +140,38 @@ def test_batch_rejects_bad_input(torch_cuda):
     with Batch([(v, e, 2)]) as b:
         with pytest.raises(PyrDGError, match="BAD_ARG"):
             b.step(1, np.array([-1.0]))
+
+
+def test_batch_replays_alternate_trace_halves(torch_cuda):
+    """FP32 batch graphs keep the face traces in a ping-pong pair across replays: one step
+    flips the current half five times, so consecutive single-step replays alternate between
+    the two captured graphs. Five replays, a projection (traces recomputed), then steps of 1 and
+    2, against single-mesh runs of the same sequence (same arithmetic: 1e-6 in FP32)."""
+    from paper_1502_07703_gb300.binding import Batch, Solver
+    meshes = _meshes()[:4]
+    with Batch(meshes, precision="f32") as b:
+        assert b.ngroups == 3
+        dt = b.dt_cfl(0.5)
+        b.project(0.0)
+        for _ in range(5):
+            b.step(1, dt)
+        mid = [b.get_state(i).astype(np.float64) for i in range(b.nmesh)]
+        b.project(0.0)
+        b.step(1, dt)
+        b.step(2, dt)
+        b.step(1, dt)
+        end = [b.get_state(i).astype(np.float64) for i in range(b.nmesh)]
+    for i, (v, e, n) in enumerate(meshes):
+        with Solver(v, e, n, precision="f32") as s:
+            s.project(0.0)
+            for _ in range(5):
+                s.step(1, dt[i])
+            U5 = s.get_state().astype(np.float64)
+            s.project(0.0)
+            s.step(1, dt[i])
+            s.step(2, dt[i])
+            s.step(1, dt[i])
+            U4 = s.get_state().astype(np.float64)
+        for got, want in ((mid[i], U5), (end[i], U4)):
+            rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+            assert rel <= 1e-6, (i, rel)
