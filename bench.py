@@ -313,6 +313,30 @@ def measure_form(binding, nx, delta, seed, n, precision, steps, warmup, dev):
                                         stage_bytes_per_element(n, 4), "achieved_gbs": gbs,
                                         "hbm_peak_gbs": HBM_GBS, "hbm_peak_kind": HBM_KIND,
                                         "hbm_frac": gbs / HBM_GBS}
+        if n >= 4:  # the same stage with the level mixing on the tensor cores (tcgen05, TF32 x 3)
+            s.set_tensor_mixing(True)
+            s.project(0.0)
+            for _ in range(warmup):
+                s.step(1, dt)
+            s.sync()
+            s.profile(True)
+            ev0.record(stream)
+            for _ in range(steps):
+                s.step(1, dt)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            s.sync()
+            ms_tc = ev0.elapsed_time(ev1)
+            prof_tc = s.profile_read()
+            s.profile(False)
+            t_tc = prof_tc["rhs"][0] / prof_tc["rhs"][1] * 1e-3
+            out["tensor_mixing"] = {
+                "ms_per_step": ms_tc / steps, "stage_kernel_ms": t_tc * 1e3,
+                "dof_updates_per_s_per_stage": s.K * s.Np * 4 * 5 * steps / (ms_tc * 1e-3),
+                "hbm_frac": stage_bytes_per_element(n, 4) * s.K / t_tc / 1e9 / HBM_GBS,
+                "note": "level mixing as tcgen05.mma kind::tf32 (A_hi B_hi + A_hi B_lo + A_lo B_hi), FP32 accumulation "
+                        "in tensor memory, one M = 128 chain per element"}
+            s.set_tensor_mixing(False)
         # error of the FP32 path as a number: 10 steps from the projected standing wave against
         # the same 10 steps of the FP64 path (which matches the FP64 oracle to <= 1e-12 in the
         # parity tests), as the L2 norm of the difference over the L2 norm of the FP64 state
@@ -320,11 +344,20 @@ def measure_form(binding, nx, delta, seed, n, precision, steps, warmup, dev):
         s.project(0.0)
         s.step(cmp_steps, dt)
         q32 = s.get_state(device=True).double()
+        if n >= 4:
+            s.set_tensor_mixing(True)
+            s.project(0.0)
+            s.step(cmp_steps, dt)
+            q32tc = s.get_state(device=True).double()
         s.close()
         with binding.Solver(v, e, n, precision="f64", bc="wall", tau=1.0, device=dev) as s64:
             s64.project(0.0)
             s64.step(cmp_steps, dt)
-            d, nb = s64.l2_diff(q32, s64.get_state(device=True))
+            q64 = s64.get_state(device=True)
+            d, nb = s64.l2_diff(q32, q64)
+            if n >= 4:
+                dtc, _ = s64.l2_diff(q32tc, q64)
+                out["tensor_mixing"]["rel_l2_vs_f64_gpu"] = dtc / nb
         out["rel_l2_vs_f64_gpu"] = {"value": d / nb, "steps": cmp_steps,
                                     "norm": "L2 over the mesh (diagonal mass matrix, pyr_dg_l2_diff)"}
         return out
@@ -510,6 +543,9 @@ def main():
     ap.add_argument("--degree", type=int, default=N, help="polynomial degree (4 = the benchmark workload)")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"],
                     help="f64 = the benchmark workload; f32 = the precision form (for profiling runs)")
+    ap.add_argument("--tensor-mixing", action="store_true",
+                    help="with --precision f32: the stage kernel with the level mixing on the tensor cores "
+                         "(for profiling runs)")
     ap.add_argument("--batch", action="store_true",
                     help="only time the batching form (256 meshes, N = 2..6, FP32) and print it as JSON "
                          "(for profiling runs)")
@@ -549,6 +585,8 @@ def main():
     v, e = make_pyramid_mesh(args.nx, delta=DELTA, seed=SEED)
     nd, prec = args.degree, args.precision
     s = binding.Solver(v, e, nd, precision=prec, bc="wall", tau=1.0, device=dev)
+    if args.tensor_mixing:
+        s.set_tensor_mixing(True)
     K, Np = s.K, s.Np
     tb = 8 if prec == "f64" else 4
     dt = s.dt_cfl(0.5)

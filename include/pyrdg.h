@@ -53,7 +53,8 @@ enum {
   PYR_DG_ERR_BAD_MESH = -2,       /* J <= 0, vertex index out of range, non-conforming face */
   PYR_DG_ERR_UNSUPPORTED_N = -3,  /* N outside [PYR_DG_MIN_N, PYR_DG_MAX_N] */
   PYR_DG_ERR_CUDA = -4,           /* CUDA runtime error (message has the CUDA string) */
-  PYR_DG_ERR_NO_MEMORY = -5       /* host or device allocation failed */
+  PYR_DG_ERR_NO_MEMORY = -5,      /* host or device allocation failed */
+  PYR_DG_ERR_TIMEOUT = -6         /* a bounded wait inside a kernel gave up (results invalid) */
 };
 
 enum { PYR_DG_MIN_N = 1, PYR_DG_MAX_N = 7 };
@@ -222,6 +223,19 @@ int pyr_dg_dt_cfl(pyr_dg* h, double cfl, double* dt);
 
 /* Current simulation time of the handle. */
 int pyr_dg_time(const pyr_dg* h, double* t);
+
+/* Single-precision stage with the level mixing (the c direction of the volume
+ * term, Sec. 4.2 Alg. 1 recast as small matrices per level) on the tensor cores:
+ * per element and RK stage, each (a, b) point's mixing inputs form one row of an
+ * M = 128 operand and one chain of tcgen05.mma kind::tf32 (FP32 accumulation in
+ * tensor memory) applies all mixing matrices at once, with the 3-term split
+ * A_hi B_hi + A_hi B_lo + A_lo B_hi for about FP32 accuracy. enable != 0 selects
+ * it, 0 the CUDA-core kernel (the default). FP32 wave handles only, else
+ * PYR_DG_ERR_BAD_ARG. One element per CTA; measured slower than the CUDA-core
+ * kernel on GB300 (the mixing is 2 to 8 terms wide, and each element waits for
+ * its MMAs). Its completion waits are bounded: pyr_dg_sync returns
+ * PYR_DG_ERR_TIMEOUT if one gave up since the last check. */
+int pyr_dg_set_tensor_mixing(pyr_dg* h, int enable);
 
 /* Wait for all work enqueued by this handle. */
 int pyr_dg_sync(pyr_dg* h);

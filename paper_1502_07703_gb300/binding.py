@@ -21,7 +21,7 @@ PYR_DG_BC_WALL, PYR_DG_BC_FREE = 0, 1
 PYR_DG_HOST, PYR_DG_DEVICE = 0, 1
 PYR_DG_WAVE, PYR_DG_ADVECTION = 0, 1
 PYR_DG_MODAL, PYR_DG_NODAL = 0, 1
-ERRORS = {-1: "BAD_ARG", -2: "BAD_MESH", -3: "UNSUPPORTED_N", -4: "CUDA", -5: "NO_MEMORY"}
+ERRORS = {-1: "BAD_ARG", -2: "BAD_MESH", -3: "UNSUPPORTED_N", -4: "CUDA", -5: "NO_MEMORY", -6: "TIMEOUT"}
 
 _lib = None
 
@@ -95,6 +95,7 @@ _SIGNATURES = {
     "pyr_dg_profile_read": (ctypes.c_int, [_c_h, _c_dp, _c_i64p, _c_dp, _c_i64p]),
     "pyr_dg_l2_diff": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_void_p, _c_dp, _c_dp]),
     "pyr_dg_host_nodal_points": (ctypes.c_int, [ctypes.c_int, _c_dp]),
+    "pyr_dg_set_tensor_mixing": (ctypes.c_int, [_c_h, ctypes.c_int]),
 }
 
 
@@ -305,6 +306,11 @@ class Solver:
         d2, n2 = ctypes.c_double(), ctypes.c_double()
         _check(lib().pyr_dg_l2_diff(self._h, qa.data_ptr(), qb.data_ptr(), ctypes.byref(d2), ctypes.byref(n2)))
         return float(np.sqrt(d2.value)), float(np.sqrt(n2.value))
+
+    def set_tensor_mixing(self, enable=True):
+        """FP32 wave handles at N >= 4: run the level mixing on the tensor cores (tcgen05 TF32,
+        3-term split) instead of the CUDA cores."""
+        _check(lib().pyr_dg_set_tensor_mixing(self._h, 1 if enable else 0))
 
     def set_error_cache(self, enable=True):
         """Store the exact fields' spatial factors for error() when they fit (the default),

@@ -217,9 +217,13 @@ int enqueue_steps(pyr_dg* h, int nsteps, double dt) {
     for (int n = 0; n < nsteps; ++n) {
       for (int s = 0; s < 5; ++s) {
         CUDA_TRY(prof_begin(h, 1, &slot));
-        h->L->stage32(h->K, h->q, h->res, buf[h->tr_cur], buf[1 - h->tr_cur], h->mapP, h->geo, h->gface, h->invM,
-                      h->bc, h->tau, kRkA[s], kRkB[s], dt, h->dt_elem, 1, h->stage_epb, h->stage_blocks,
-                      h->stream);
+        if (h->use_tc)
+          h->L->stage32tc(h->K, h->q, h->res, buf[h->tr_cur], buf[1 - h->tr_cur], h->mapP, h->geo, h->gface,
+                          h->invM, h->bc, h->tau, kRkA[s], kRkB[s], dt, h->dt_elem, 1, h->stage_blocks, h->stream);
+        else
+          h->L->stage32(h->K, h->q, h->res, buf[h->tr_cur], buf[1 - h->tr_cur], h->mapP, h->geo, h->gface,
+                        h->invM, h->bc, h->tau, kRkA[s], kRkB[s], dt, h->dt_elem, 1, h->stage_epb, h->stage_blocks,
+                        h->stream);
         CUDA_TRY(prof_end(h, slot));
         h->tr_cur = 1 - h->tr_cur;
       }
@@ -824,6 +828,40 @@ int pyr_dg_sync(pyr_dg* h) {
   DeviceGuard g(h->device);
   CUDA_TRY(g.err);
   CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (h->use_tc) {
+    const int n = h->L->tc32_timeouts();
+    if (n < 0) return fail(PYR_DG_ERR_CUDA, "cannot read the tensor-core wait counter");
+    if (n > 0) return fail(PYR_DG_ERR_TIMEOUT, "%d tensor-core completion wait(s) gave up", n);
+  }
+  return PYR_DG_OK;
+}
+
+int pyr_dg_set_tensor_mixing(pyr_dg* h, int enable) {
+  if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
+  if (!enable) {
+    if (h->use_tc) {
+      h->use_tc = false;
+      int nsm = 1;
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+      h->stage_epb = h->L->epb32;
+      const int64_t groups = (h->K + h->stage_epb - 1) / h->stage_epb;
+      h->stage_blocks = (int)std::min<int64_t>(groups, (int64_t)nsm * h->L->blocks_per_sm32(h->stage_epb));
+    }
+    return PYR_DG_OK;
+  }
+  if (!h->use_stage32 || h->equation != PYR_DG_WAVE || !h->L->stage32tc)
+    return fail(PYR_DG_ERR_BAD_ARG, "tensor-core mixing needs an FP32 wave handle");
+  DeviceGuard g(h->device);
+  CUDA_TRY(g.err);
+  int nsm = 1;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  const int bps = h->L->blocks_per_sm32tc();
+  if (bps <= 0)
+    return fail(PYR_DG_ERR_CUDA, "occupancy of the tensor-core stage kernel: %s",
+                cudaGetErrorString((cudaError_t)(-bps)));
+  h->use_tc = true;
+  h->stage_epb = 1;
+  h->stage_blocks = (int)std::min<int64_t>(h->K, (int64_t)nsm * bps);
   return PYR_DG_OK;
 }
 

@@ -37,6 +37,7 @@ struct pyr_dg {
   void* tr2 = nullptr;
   int tr_cur = 0;
   bool tr_valid = false;
+  bool use_tc = false;          // FP32 stage with the tensor-core level mixing (pyr_dg_set_tensor_mixing)
   int stage_blocks = 0;         // persistent grid of the FP32 stage kernel
   int stage_epb = 1;            // elements per CTA of the FP32 stage kernel
   // per-element time step (device, K elements of the handle's type) when the handle

@@ -168,6 +168,47 @@ struct Impl {
           (const float*)dt_elem, write_traces);
     }
   }
+  static constexpr bool kTC = sizeof(T) == 4;  // tensor-core mixing (FP32 handles)
+  static void stage32tc(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
+                        const void* geo, const void* gface, const void* invM, int bc, double tau, double rka,
+                        double rkb, double dt, const void* dt_elem, int write_traces, int nblocks, cudaStream_t s) {
+    if constexpr (kTC) {
+      static_assert(S32<N, 1, true>::bytes <= kMaxSmem, "FP32 tensor-core stage kernel shared memory");
+      stage32_kernel<N, 1, true><<<nblocks, S32<N, 1, true>::NT, S32<N, 1, true>::bytes, s>>>(
+          K, (float*)q, (float*)res, (const float*)tr_cur, (float*)tr_nxt, mapP, (const float*)geo,
+          (const float*)gface, (const float*)invM, bc, (float)tau, (float)rka, (float)rkb, (float)dt,
+          (const float*)dt_elem, write_traces);
+    }
+  }
+  // Resident CTAs per SM of the tensor-core variant from its registers and shared memory, or
+  // minus a CUDA error. The occupancy calculator reports one CTA per SM for kernels that use
+  // tcgen05 (it does not know how much tensor memory they allocate); this kernel allocates 32
+  // of the 512 TMEM columns per CTA, so registers and shared memory are the real limits.
+  static int blocks_per_sm32tc() {
+    if constexpr (kTC) {
+      cudaFuncAttributes a;
+      cudaError_t e = cudaFuncGetAttributes(&a, stage32_kernel<N, 1, true>);
+      int dev = 0, regs = 0, smem = 0, resv = 0;
+      if (e == cudaSuccess) e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+      if (e != cudaSuccess) return -(int)e;
+      const int by_regs = regs / (((a.numRegs + 7) / 8 * 8) * 128);
+      const int by_smem = smem / ((int)S32<N, 1, true>::bytes + resv);
+      const int n = std::min(std::min(by_regs, by_smem), 16);
+      return n > 0 ? n : 1;
+    }
+    return 0;
+  }
+  static int tc32_timeouts() {
+    int n = 0, zero = 0;
+    if constexpr (kTC) {
+      if (cudaMemcpyFromSymbol(&n, g_tc32_timeouts, sizeof(int)) != cudaSuccess) return -1;
+      if (n != 0 && cudaMemcpyToSymbol(g_tc32_timeouts, &zero, sizeof(int)) != cudaSuccess) return -1;
+    }
+    return n;
+  }
   // epb must be one blocks_per_sm32 reports as built (nonzero)
   static void stage32(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
                       const void* geo, const void* gface, const void* invM, int bc, double tau, double rka, double rkb,
@@ -280,6 +321,10 @@ struct Impl {
     if (e == cudaSuccess) e = smem_adv32<2>();
     if (e == cudaSuccess) e = smem_adv32<4>();
     if (e == cudaSuccess) e = smem_adv32<8>();
+    if constexpr (kTC)
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stage32_kernel<N, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)S32<N, 1, true>::bytes);
     return e;
   }
   // Resident CTAs per SM of the stage kernel with epb elements per CTA; 0 if not built.
@@ -312,6 +357,9 @@ struct Impl {
     l.rhs1 = &rhs1;
     l.project1 = &project1;
     l.error1 = &error1;
+    l.stage32tc = kTC ? &stage32tc : nullptr;
+    l.blocks_per_sm32tc = kTC ? &blocks_per_sm32tc : nullptr;
+    l.tc32_timeouts = kTC ? &tc32_timeouts : nullptr;
     l.nodal_ntr = NodalDims<N>::NTR;
     l.nodal_ntab = NodalDims<N>::size;
     l.nodal_trace = sizeof(T) == 8 ? &nodal_trace : nullptr;

@@ -72,6 +72,14 @@ struct Launchers {
                     const void* geo, const void* gface, const void* invM, const void* tab, const double* ntab,
                     const int32_t* tri_node, int bc, double tau, double rka, double rkb, double dt, int update,
                     cudaStream_t s);
+  // FP32 stage kernel with the level mixing on the tensor cores (tcgen05, TF32 3-term split),
+  // one element per CTA; null for double. Arguments as stage32's.
+  void (*stage32tc)(int64_t K, void* q, void* res, const void* tr_cur, void* tr_nxt, const int32_t* mapP,
+                    const void* geo, const void* gface, const void* invM, int bc, double tau, double rka, double rkb,
+                    double dt, const void* dt_elem, int write_traces, int nblocks, cudaStream_t s);
+  int (*blocks_per_sm32tc)();
+  // Read and clear the count of its completion waits that gave up (0 in normal operation).
+  int (*tc32_timeouts)();
   int nodal_ntr;      // trace points per element of the nodal variant
   int nodal_ntab;     // doubles in its table
 };

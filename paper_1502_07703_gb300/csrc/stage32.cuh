@@ -19,6 +19,7 @@
 #pragma once
 
 #include "dg_kernels.cuh"
+#include "tc32.cuh"
 
 namespace pyrdg {
 
@@ -70,7 +71,7 @@ constexpr bool epb_supported(int N, int EPB) {
 }
 
 // Shared-memory layout and work decomposition for degree N with EPB elements per CTA.
-template <int N, int EPB>
+template <int N, int EPB, bool TC = false>
 struct S32 {
   using d = Dims<N>;
   static constexpr int NT = 128;
@@ -100,26 +101,140 @@ struct S32 {
   static constexpr size_t ZA = 4 * d::nrow * YS > 8 * d::nrow * d::n1 ? 4 * d::nrow * YS : 8 * d::nrow * d::n1;
   static constexpr size_t A = Fs + EPB * 4 * d::Nfc;             // EPB x ZA: A, dA as [row][p][f], later Z, At
   static constexpr size_t Y = A + EPB * ZA;                      // EPB x 4 n1 nY  [f][k][p'][q']
-  static constexpr size_t total = Y + EPB * 4 * d::n1 * nY;
+  static constexpr size_t total0 = Y + EPB * 4 * d::n1 * nY;
+  // Tensor-core level mixing (TC, one element per CTA): the mixing inputs of every (a, b)
+  // point form one row of an M = 128 TF32 operand tile, row = thread: velocity-half rows
+  // hold [Zc | X] in columns [0, 2 n1), pressure-half rows [U0 | Ua0 | Ub0] in [2 n1, 5 n1),
+  // other entries zero. B holds the mixing matrices (velocity outputs Y_p in columns
+  // [0, n1), then G, alpha, beta of the pressure half in [n1, 4 n1)). The tile aliases the
+  // A/dA and Y regions when they are large enough (their contents are dead or rewritten while
+  // it is in use), else it follows them; B (hi and lo parts) and the mbarrier come last.
+  static constexpr int KT = (5 * d::n1 + 7) / 8 * 8;      // K of the MMA (multiple of 8 for kind::tf32)
+  static constexpr int NPT = (4 * d::n1 + 15) / 16 * 16;  // N of the MMA (multiple of 16 at M = 128)
+  static constexpr bool TC_ALIAS = 128 * KT <= EPB * ZA + EPB * 4 * d::n1 * nY;
+  static constexpr size_t tcA = TC_ALIAS ? A : total0;
+  static constexpr size_t tcBh = TC_ALIAS ? total0 : total0 + 128 * KT;
+  static constexpr size_t tcBl = tcBh + NPT * KT;
+  static constexpr size_t tcbar = tcBl + NPT * KT;        // mbarrier (2 words), TMEM address, timeout flag
+  static constexpr size_t total = TC ? tcbar + 4 : total0;
+  static_assert(!TC || EPB == 1, "tensor-core mixing: one element per CTA");
+  static_assert(!TC || 4 * d::n1 <= 32, "tensor-core mixing: at most 32 accumulator columns");
   static_assert(4 * d::nrow * d::P3 <= ZA, "trace a pass (At) aliases the A/dA region");
   static_assert(MIXT <= NT, "mixing slots");
   // resident CTAs per SM the register budget is tuned for (at N = 6, 5 CTAs with 96
-  // registers run faster than 4 with 127; N = 7 is held to 4 by shared memory)
-  static constexpr int MIN_BLOCKS = N <= 5 ? 8 : 5;
+  // registers run faster than 4 with 127; N = 7 is held to 4 by shared memory); the
+  // tensor-core variant is held to fewer by its shared memory, so it may use more registers
+  static constexpr int MIN_BLOCKS_CC = N <= 5 ? 8 : 5;
+  static constexpr int SMEM_BLOCKS = (int)((227 * 1024) / (total * sizeof(float)));
+  static constexpr int MIN_BLOCKS = TC && SMEM_BLOCKS < MIN_BLOCKS_CC ? (SMEM_BLOCKS > 0 ? SMEM_BLOCKS : 1)
+                                                                      : MIN_BLOCKS_CC;
   // L2 prefetch of the next element's own and neighbour traces and connectivity: used at
   // N >= 6, where each element's flux gathers are longest
   static constexpr bool PREFETCH = N >= 6 && EPB == 1;
   static constexpr size_t bytes = total * sizeof(float);
 };
 
-template <int N, int EPB>
-__global__ void __launch_bounds__(128, S32<N, EPB>::MIN_BLOCKS)
+// Inputs of the velocity half's level mixing at the (a_p, b_q) point: per level k,
+// X[k] = sum_m (g1_m (u_m)_a + g2_m (u_m)_b) and Zc[k] = sum_m g3_m u_m from the a-pass
+// output (A, dA as [row][p][field]) and the b-direction tables; g: the point's 9 factors.
+template <int N>
+__device__ __forceinline__ void mix_velocity_inputs(const float* s_A, const float* s_dA, const float* s_lx,
+                                                    const float* s_dl, const float* g, int p, int qq, float* X,
+                                                    float* Zc) {
+  using d = Dims<N>;
+  constexpr int n1 = d::n1, P3 = d::P3;
+#pragma unroll
+  for (int k = 0; k <= N; ++k) {
+    float lq[n1], dlq[n1];
+#pragma unroll
+    for (int j = 0; j <= k; ++j) {
+      if (k < N) lq[j] = s_lx[(tri_num(k) + j) * P3 + qq];
+      dlq[j] = s_dl[(tri_num(k) + j) * n1 + qq];
+    }
+    // the three velocity fields of A, dA at (row, p) in one float4 each
+    float v[3] = {0.f, 0.f, 0.f}, va[3] = {0.f, 0.f, 0.f}, vb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j <= k; ++j) {
+      const int o = ((tri_num(k) + j) * n1 + p) * 4;
+      const float4 a4 = *reinterpret_cast<const float4*>(s_A + o);
+      const float a3[3] = {a4.y, a4.z, a4.w};
+#pragma unroll
+      for (int m = 0; m < 3; ++m) vb[m] = fmaf(a3[m], dlq[j], vb[m]);
+      if (k < N) {
+        const float4 d4 = *reinterpret_cast<const float4*>(s_dA + o);
+        const float d3[3] = {d4.y, d4.z, d4.w};
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          v[m] = fmaf(a3[m], lq[j], v[m]);
+          va[m] = fmaf(d3[m], lq[j], va[m]);
+        }
+      }
+    }
+    if (k == N) {  // l_j^N(b_q) = delta_jq
+      const int o = ((tri_num(k) + qq) * n1 + p) * 4;
+      const float4 a4 = *reinterpret_cast<const float4*>(s_A + o);
+      const float4 d4 = *reinterpret_cast<const float4*>(s_dA + o);
+      v[0] = a4.y, v[1] = a4.z, v[2] = a4.w;
+      va[0] = d4.y, va[1] = d4.z, va[2] = d4.w;
+    }
+    float xs = 0.f, zs = 0.f;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      xs = fmaf(g[m], va[m], fmaf(g[3 + m], vb[m], xs));
+      zs = fmaf(g[6 + m], v[m], zs);
+    }
+    X[k] = xs;
+    Zc[k] = zs;
+  }
+}
+
+// Inputs of the pressure half's level mixing at (a_p, b_q): per level k the value U0, the
+// a-derivative Ua0 and the b-derivative Ub0 of p.
+template <int N>
+__device__ __forceinline__ void mix_pressure_inputs(const float* s_A, const float* s_dA, const float* s_lx,
+                                                    const float* s_dl, int p, int qq, float* U0, float* Ua0,
+                                                    float* Ub0) {
+  using d = Dims<N>;
+  constexpr int n1 = d::n1, P3 = d::P3;
+#pragma unroll
+  for (int k = 0; k <= N; ++k) {
+    float u = 0.f, ua = 0.f, ub = 0.f;
+#pragma unroll
+    for (int j = 0; j <= k; ++j) {
+      const int o = ((tri_num(k) + j) * n1 + p) * 4;
+      const float a = s_A[o];
+      ub = fmaf(a, s_dl[(tri_num(k) + j) * n1 + qq], ub);
+      if (k < N) {
+        const float lq = s_lx[(tri_num(k) + j) * P3 + qq];
+        u = fmaf(a, lq, u);
+        ua = fmaf(s_dA[o], lq, ua);
+      }
+    }
+    if (k == N) {  // l_j^N(b_q) = delta_jq
+      const int o = ((tri_num(k) + qq) * n1 + p) * 4;
+      u = s_A[o];
+      ua = s_dA[o];
+    }
+    U0[k] = u;
+    Ua0[k] = ua;
+    Ub0[k] = ub;
+  }
+}
+
+// Polls of the tensor-core completion wait before the stage kernel gives up and counts a
+// timeout (each poll may suspend for a bounded time): far beyond an MMA's microseconds.
+constexpr int kTcWaitPolls = 1 << 20;
+// Timeouts of the tensor-core mixing's waits since the host last read and cleared them.
+static __device__ int g_tc32_timeouts;
+
+template <int N, int EPB, bool TC = false>
+__global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
     stage32_kernel(int64_t K, float* __restrict__ q, float* __restrict__ res, const float* __restrict__ tr_cur,
                     float* __restrict__ tr_nxt, const int32_t* __restrict__ mapP, const float* __restrict__ geo,
                     const float* __restrict__ gface, const float* __restrict__ invM, int bc, float tau, float rka,
                     float rkb, float dt, const float* __restrict__ dt_elem, int write_traces) {
   using d = Dims<N>;
-  using S = S32<N, EPB>;
+  using S = S32<N, EPB, TC>;
   using C = C32<N>;
   constexpr int n1 = d::n1, n2 = d::n2, P3 = d::P3, nrow = d::nrow, Np = d::Np, Nfc = d::Nfc;
   constexpr int YS = S::YS, nY = S::nY, ZA = (int)S::ZA;
@@ -141,6 +256,42 @@ __global__ void __launch_bounds__(128, S32<N, EPB>::MIN_BLOCKS)
   for (int x = tid; x < nrow * n1; x += S::NT) s_dl[x] = c32[C::DL + x];
   // Y entries that no pass writes (face rows x face columns) stay zero
   for (int x = tid; x < EPB * 4 * n1 * nY; x += S::NT) s_Y0[x] = 0.f;
+  // tensor-core mixing: B tiles (TF32 hi and lo parts of the mixing matrices), the mbarrier
+  // the MMAs complete on, and 32 TMEM columns for the accumulators
+  uint32_t tmem = 0, mbar = 0;
+  bool tc_ok = true;
+  uint32_t* tc_flag = nullptr;  // set to 1 once a completion wait gave up
+  if constexpr (TC) {
+    constexpr int KT = S::KT;
+    float* Bh = sm + S::tcBh;
+    float* Bl = sm + S::tcBl;
+    for (int x = tid; x < S::NPT * KT; x += S::NT) {
+      const int n = x / KT, k = x - n * KT;
+      float v = 0.f;
+      const int kp = n % n1, kk = k % n1;  // output level k', input level k
+      if (n < n1 && k < n1) v = c32[C::MG + kp * n1 + kk];                          // Y_p <- Zc (c derivative)
+      else if (n < n1 && k < 2 * n1) v = c32[C::MH + kp * n1 + kk];                 // Y_p <- X (r, s derivatives)
+      else if (n >= n1 && n < 2 * n1 && k >= 2 * n1 && k < 3 * n1) v = c32[C::MG + kp * n1 + kk];  // G <- U
+      else if (n >= 2 * n1 && n < 3 * n1 && k >= 3 * n1 && k < 4 * n1) v = c32[C::MH + kp * n1 + kk];  // alpha <- U_a
+      else if (n >= 3 * n1 && n < 4 * n1 && k >= 4 * n1 && k < 5 * n1) v = c32[C::MH + kp * n1 + kk];  // beta <- U_b
+      float hi, lo;
+      tf32_split(v, hi, lo);
+      Bh[tc_offset<KT>(n, k)] = hi;
+      Bl[tc_offset<KT>(n, k)] = lo;
+    }
+    uint32_t* bar = reinterpret_cast<uint32_t*>(sm + S::tcbar);
+    mbar = smem_addr(bar);
+    tc_flag = bar + 3;
+    if (tid == 0) {
+      tc_mbar_init(mbar, 1);
+      *tc_flag = 0u;
+    }
+    if (tid < 32) tc_alloc(bar + 2, 32);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    tmem = bar[2];
+  }
 
   // Element ei of the group starting at e0. Every pass works on all EPB elements, so its
   // item counts are compile-time constants; past the end of the mesh (the last group)
@@ -249,118 +400,177 @@ __global__ void __launch_bounds__(128, S32<N, EPB>::MIN_BLOCKS)
     // ---- level mixing (c direction of Alg. 1) per (element, a, b point), base lift;
     // triangle-face c^T. Two warp-aligned halves: the velocity half forms div(u) and
     // feeds the p equation, the pressure half forms grad(p) and feeds the velocity equations.
-    if (tid < S::MIXT) {
+    if constexpr (TC) {
+      // Tensor-core form (one element per CTA): every thread's mixing inputs become row tid of
+      // the TF32 operand tile (zeros outside its half and for idle threads), and one chain of
+      // M = 128, N = NPT, K = KT MMAs forms all outputs at once:
+      // D = A_hi B_hi + A_hi B_lo + A_lo B_hi (the 3-term split, about FP32 accuracy), in two
+      // phases through the one tile: hi parts first, then lo parts once the first MMAs are done.
+      constexpr int KT = S::KT;
       const int half = tid / (S::WV * 32);
       const int y = tid - half * S::WV * 32;
-      if (y < EPB * n2) {
-        const int ei = EPB == 1 ? 0 : y / n2, pq = y - ei * n2;
-        const int p = pq % n1, qq = pq / n1;
-        const float* g = bcur + ei * S::bsz + S::bgeo + pq * d::NGEO;
-        const float* s_A = s_A0 + ei * ZA;
-        const float* s_dA = s_A + 4 * nrow * n1;
-        const float* s_Fs = s_Fs0 + ei * 4 * Nfc;
-        float* s_Y = s_Y0 + ei * 4 * n1 * nY;
+      const bool act = tid < S::MIXT && y < n2;
+      const int pq = act ? y : 0, p = pq % n1, qq = pq / n1;
+      const float* g = bcur + S::bgeo + pq * d::NGEO;
+      float kv[5 * n1];
+#pragma unroll
+      for (int c = 0; c < 5 * n1; ++c) kv[c] = 0.f;
+      if (act) {
+        if (half == 0)
+          mix_velocity_inputs<N>(s_A0, s_A0 + 4 * nrow * n1, s_lx, s_dl, g, p, qq, kv + n1, kv);
+        else
+          mix_pressure_inputs<N>(s_A0, s_A0 + 4 * nrow * n1, s_lx, s_dl, p, qq, kv + 2 * n1, kv + 3 * n1,
+                                 kv + 4 * n1);
+      }
+      if (S::TC_ALIAS) __syncthreads();  // the tile overwrites A/dA, which the inputs came from
+      float* tA = sm + S::tcA;
+      const uint32_t a0 = smem_addr(tA), bh0 = smem_addr(sm + S::tcBh), bl0 = smem_addr(sm + S::tcBl);
+      constexpr uint32_t idesc = tc_idesc_tf32(128, S::NPT);
+#pragma unroll
+      for (int c4 = 0; c4 < KT / 4; ++c4) {  // phase 1: hi parts; kv keeps the lo parts
+        float h[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = 4 * c4 + i;
+          float lo = 0.f;
+          h[i] = 0.f;
+          if (c < 5 * n1) {
+            tf32_split(kv[c], h[i], lo);
+            kv[c] = lo;
+          }
+        }
+        *reinterpret_cast<float4*>(tA + tc_offset<KT>(tid, 4 * c4)) = make_float4(h[0], h[1], h[2], h[3]);
+      }
+      tc_fence_smem();
+      __syncthreads();
+      if (tid == 0 && tc_ok) {
+        tc_fence_after();
+#pragma unroll
+        for (int st = 0; st < KT / 8; ++st)
+          tc_mma_tf32(tmem, tc_smem_desc(a0 + 256 * st, 128, 32 * KT), tc_smem_desc(bh0 + 256 * st, 128, 32 * KT),
+                      idesc, st > 0);
+#pragma unroll
+        for (int st = 0; st < KT / 8; ++st)
+          tc_mma_tf32(tmem, tc_smem_desc(a0 + 256 * st, 128, 32 * KT), tc_smem_desc(bl0 + 256 * st, 128, 32 * KT),
+                      idesc, true);
+        tc_commit(mbar);
+      }
+      // the issuing thread waits for completion and the CTA barrier releases the rest; once a
+      // wait has given up (results flagged invalid) no further MMA is issued or waited for, so a
+      // stuck tensor core costs one bounded wait, not one per element
+      if (tid == 0 && tc_ok && !tc_mbar_wait(mbar, 0, kTcWaitPolls)) tc_flag[0] = 1u;
+      __syncthreads();
+      tc_ok = tc_flag[0] == 0u;
+      tc_fence_after();
+#pragma unroll
+      for (int c4 = 0; c4 < KT / 4; ++c4) {  // phase 2: lo parts
+        float l[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) l[i] = 4 * c4 + i < 5 * n1 ? kv[4 * c4 + i] : 0.f;
+        *reinterpret_cast<float4*>(tA + tc_offset<KT>(tid, 4 * c4)) = make_float4(l[0], l[1], l[2], l[3]);
+      }
+      tc_fence_smem();
+      __syncthreads();
+      if (tid == 0 && tc_ok) {
+        tc_fence_after();
+#pragma unroll
+        for (int st = 0; st < KT / 8; ++st)
+          tc_mma_tf32(tmem, tc_smem_desc(a0 + 256 * st, 128, 32 * KT), tc_smem_desc(bh0 + 256 * st, 128, 32 * KT),
+                      idesc, true);
+        tc_commit(mbar);
+      }
+      if (tid == 0 && tc_ok && !tc_mbar_wait(mbar, 1, kTcWaitPolls)) tc_flag[0] = 1u;
+      __syncthreads();
+      tc_ok = tc_flag[0] == 0u;
+      tc_fence_after();
+      // accumulators: warp w reads TMEM lanes 32 w .. 32 w + 31, i.e. its own threads' rows
+      float acc[24];
+      const int warp = tid >> 5;
+      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+      if (warp < S::WV) {
+        tc_ld8(tl, acc);
+      } else if (warp < 2 * S::WV) {
+        tc_ld16(tl + n1, acc);
+        tc_ld8(tl + n1 + 16, acc + 16);
+      }
+      tc_wait_ld();
+      tc_fence_before();  // these loads precede the next element's MMAs (issued after barriers)
+      if (act) {
         if (half == 0) {
-          float X[n1], Zc[n1];
+          const float Fb = s_Fs0[pq];
 #pragma unroll
-          for (int k = 0; k <= N; ++k) {
-            float lq[n1], dlq[n1];
-#pragma unroll
-            for (int j = 0; j <= k; ++j) {
-              if (k < N) lq[j] = s_lx[(tri_num(k) + j) * P3 + qq];
-              dlq[j] = s_dl[(tri_num(k) + j) * n1 + qq];
-            }
-            // the three velocity fields of A, dA at (row, p) in one float4 each
-            float v[3] = {0.f, 0.f, 0.f}, va[3] = {0.f, 0.f, 0.f}, vb[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int j = 0; j <= k; ++j) {
-              const int o = ((tri_num(k) + j) * n1 + p) * 4;
-              const float4 a4 = *reinterpret_cast<const float4*>(s_A + o);
-              const float a3[3] = {a4.y, a4.z, a4.w};
-#pragma unroll
-              for (int m = 0; m < 3; ++m) vb[m] = fmaf(a3[m], dlq[j], vb[m]);
-              if (k < N) {
-                const float4 d4 = *reinterpret_cast<const float4*>(s_dA + o);
-                const float d3[3] = {d4.y, d4.z, d4.w};
-#pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                  v[m] = fmaf(a3[m], lq[j], v[m]);
-                  va[m] = fmaf(d3[m], lq[j], va[m]);
-                }
-              }
-            }
-            if (k == N) {  // l_j^N(b_q) = delta_jq
-              const int o = ((tri_num(k) + qq) * n1 + p) * 4;
-              const float4 a4 = *reinterpret_cast<const float4*>(s_A + o);
-              const float4 d4 = *reinterpret_cast<const float4*>(s_dA + o);
-              v[0] = a4.y, v[1] = a4.z, v[2] = a4.w;
-              va[0] = d4.y, va[1] = d4.z, va[2] = d4.w;
-            }
-            float xs = 0.f, zs = 0.f;
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-              xs = fmaf(g[m], va[m], fmaf(g[3 + m], vb[m], xs));
-              zs = fmaf(g[6 + m], v[m], zs);
-            }
-            X[k] = xs;
-            Zc[k] = zs;
-          }
-          const float Fb = s_Fs[pq];
-#pragma unroll
-          for (int kp = 0; kp <= N; ++kp) {
-            float dv = 0.f;
-#pragma unroll
-            for (int k = 0; k <= N; ++k) {  // MG lower Hessenberg, MH tridiagonal
-              if (k > kp + 1) continue;
-              dv = fmaf(c32[C::MG + kp * n1 + k], Zc[k], dv);
-              if (k >= kp - 1) dv = fmaf(c32[C::MH + kp * n1 + k], X[k], dv);
-            }
-            s_Y[kp * nY + p * YS + qq] = fmaf(c32[C::GB + kp], Fb, dv);
-          }
+          for (int kp = 0; kp <= N; ++kp) s_Y0[kp * nY + p * YS + qq] = fmaf(c32[C::GB + kp], Fb, acc[kp]);
         } else {
-          float U0[n1], Ua0[n1], Ub0[n1];
-#pragma unroll
-          for (int k = 0; k <= N; ++k) {
-            float u = 0.f, ua = 0.f, ub = 0.f;
-#pragma unroll
-            for (int j = 0; j <= k; ++j) {
-              const int o = ((tri_num(k) + j) * n1 + p) * 4;
-              const float a = s_A[o];
-              ub = fmaf(a, s_dl[(tri_num(k) + j) * n1 + qq], ub);
-              if (k < N) {
-                const float lq = s_lx[(tri_num(k) + j) * P3 + qq];
-                u = fmaf(a, lq, u);
-                ua = fmaf(s_dA[o], lq, ua);
-              }
-            }
-            if (k == N) {  // l_j^N(b_q) = delta_jq
-              const int o = ((tri_num(k) + qq) * n1 + p) * 4;
-              u = s_A[o];
-              ua = s_dA[o];
-            }
-            U0[k] = u;
-            Ua0[k] = ua;
-            Ub0[k] = ub;
-          }
           float Fb[3];
 #pragma unroll
-          for (int m = 0; m < 3; ++m) Fb[m] = s_Fs[(m + 1) * Nfc + pq];
+          for (int m = 0; m < 3; ++m) Fb[m] = s_Fs0[(m + 1) * Nfc + pq];
 #pragma unroll
           for (int kp = 0; kp <= N; ++kp) {
-            float al = 0.f, be = 0.f, ga = 0.f;
-#pragma unroll
-            for (int k = 0; k <= N; ++k) {  // MG lower Hessenberg, MH tridiagonal
-              if (k > kp + 1) continue;
-              ga = fmaf(c32[C::MG + kp * n1 + k], U0[k], ga);
-              if (k < kp - 1) continue;
-              al = fmaf(c32[C::MH + kp * n1 + k], Ua0[k], al);
-              be = fmaf(c32[C::MH + kp * n1 + k], Ub0[k], be);
-            }
+            const float ga = acc[kp], al = acc[n1 + kp], be = acc[2 * n1 + kp];
             const float gb = c32[C::GB + kp];
             const int yo = kp * nY + p * YS + qq;
 #pragma unroll
             for (int m = 0; m < 3; ++m)
-              s_Y[(m + 1) * n1 * nY + yo] = fmaf(gb, Fb[m], fmaf(g[m], al, fmaf(g[3 + m], be, g[6 + m] * ga)));
+              s_Y0[(m + 1) * n1 * nY + yo] = fmaf(gb, Fb[m], fmaf(g[m], al, fmaf(g[3 + m], be, g[6 + m] * ga)));
+          }
+        }
+      }
+      if (S::TC_ALIAS) {  // face rows x face columns of Y, which no pass writes: the tile overwrote them
+        for (int x = tid; x < 16 * n1; x += S::NT) {
+          const int f = x / (4 * n1), k = (x / 4) % n1, ij = x % 4;
+          s_Y0[(f * n1 + k) * nY + (n1 + ij / 2) * YS + n1 + ij % 2] = 0.f;
+        }
+      }
+    } else {
+      if (tid < S::MIXT) {
+        const int half = tid / (S::WV * 32);
+        const int y = tid - half * S::WV * 32;
+        if (y < EPB * n2) {
+          const int ei = EPB == 1 ? 0 : y / n2, pq = y - ei * n2;
+          const int p = pq % n1, qq = pq / n1;
+          const float* g = bcur + ei * S::bsz + S::bgeo + pq * d::NGEO;
+          const float* s_A = s_A0 + ei * ZA;
+          const float* s_dA = s_A + 4 * nrow * n1;
+          const float* s_Fs = s_Fs0 + ei * 4 * Nfc;
+          float* s_Y = s_Y0 + ei * 4 * n1 * nY;
+          if (half == 0) {
+            float X[n1], Zc[n1];
+            mix_velocity_inputs<N>(s_A, s_dA, s_lx, s_dl, g, p, qq, X, Zc);
+            const float Fb = s_Fs[pq];
+#pragma unroll
+            for (int kp = 0; kp <= N; ++kp) {
+              float dv = 0.f;
+#pragma unroll
+              for (int k = 0; k <= N; ++k) {  // MG lower Hessenberg, MH tridiagonal
+                if (k > kp + 1) continue;
+                dv = fmaf(c32[C::MG + kp * n1 + k], Zc[k], dv);
+                if (k >= kp - 1) dv = fmaf(c32[C::MH + kp * n1 + k], X[k], dv);
+              }
+              s_Y[kp * nY + p * YS + qq] = fmaf(c32[C::GB + kp], Fb, dv);
+            }
+          } else {
+            float U0[n1], Ua0[n1], Ub0[n1];
+            mix_pressure_inputs<N>(s_A, s_dA, s_lx, s_dl, p, qq, U0, Ua0, Ub0);
+            float Fb[3];
+#pragma unroll
+            for (int m = 0; m < 3; ++m) Fb[m] = s_Fs[(m + 1) * Nfc + pq];
+#pragma unroll
+            for (int kp = 0; kp <= N; ++kp) {
+              float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+              for (int k = 0; k <= N; ++k) {  // MG lower Hessenberg, MH tridiagonal
+                if (k > kp + 1) continue;
+                ga = fmaf(c32[C::MG + kp * n1 + k], U0[k], ga);
+                if (k < kp - 1) continue;
+                al = fmaf(c32[C::MH + kp * n1 + k], Ua0[k], al);
+                be = fmaf(c32[C::MH + kp * n1 + k], Ub0[k], be);
+              }
+              const float gb = c32[C::GB + kp];
+              const int yo = kp * nY + p * YS + qq;
+#pragma unroll
+              for (int m = 0; m < 3; ++m)
+                s_Y[(m + 1) * n1 * nY + yo] = fmaf(gb, Fb[m], fmaf(g[m], al, fmaf(g[3 + m], be, g[6 + m] * ga)));
+            }
           }
         }
       }
@@ -537,6 +747,17 @@ __global__ void __launch_bounds__(128, S32<N, EPB>::MIN_BLOCKS)
         }
       }
     }
+  }
+  if constexpr (TC) {
+    // a wait that gave up leaves its MMAs possibly in flight: wait for the last phase once more
+    // (returns at once when every phase completed or none was issued), then free the TMEM
+    if (!tc_ok && tid == 0) {
+      atomicAdd(&g_tc32_timeouts, 1);
+      tc_mbar_wait(mbar, 1, kTcWaitPolls);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid < 32) tc_dealloc(tmem, 32);
   }
 }
 
