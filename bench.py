@@ -443,7 +443,7 @@ def measure_advection(binding, nx, n, precision, steps, warmup, dev):
     return out
 
 
-def measure_batch(binding, steps, warmup, dev, count=256):
+def measure_batch(binding, steps, warmup, dev, count=256, alone=True):
     """Batching form: `count` independent meshes (sizes log-uniform 48..49,152 pyramids,
     degrees uniform in 2..6, seed 2), FP32, each with its own CFL time step, advanced by
     one graph-captured batch step per call."""
@@ -471,13 +471,37 @@ def measure_batch(binding, steps, warmup, dev, count=256):
     b.sync()
     ms = ev0.elapsed_time(ev1)
     _, rel = b.error()
+    groups = b.groups()
+    b.close()
+    # the same meshes one degree at a time: the sum of these step times is what the batch
+    # would take if its degree groups ran one after another with no overlap and no tail
+    alone_t = []
+    for deg in (sorted(set(int(n) for n in b.N)) if alone else []):
+        sub = [m for m in meshes if m[2] == deg]
+        bs = binding.Batch(sub, precision="f32", device=dev)
+        dts = bs.dt_cfl(0.5)
+        bs.project(0.0)
+        st = torch.cuda.ExternalStream(bs.stream_ptr, device=dev)
+        for _ in range(warmup):
+            bs.step(1, dts)
+        bs.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            bs.step(1, dts)
+        e1.record(st)
+        bs.sync()
+        alone_t.append({"N": deg, "meshes": len(sub), "ms_per_step": e0.elapsed_time(e1) / steps})
+        bs.close()
+    ideal = sum(a["ms_per_step"] for a in alone_t) if alone_t else None
     out = {"meshes": count, "K_total": int(b.total_K), "dofs_total": int(b.total_dofs),
            "K_min": int(b.K.min()), "K_max": int(b.K.max()), "degrees": sorted(set(int(n) for n in b.N)),
-           "launches_per_stage": b.ngroups, "groups": b.groups(), "precision": "f32", "steps": steps,
+           "launches_per_stage": b.ngroups, "groups": groups, "precision": "f32", "steps": steps,
            "ms_per_step": ms / steps, "dof_updates_per_s_per_stage": b.total_dofs * 5 * steps / (ms * 1e-3),
            "l2_rel_error_vs_exact_max": float(rel.max()),
+           "degree_groups_alone": alone_t, "sum_of_groups_alone_ms_per_step": ideal,
+           "batch_over_sum_of_groups_alone": (ms / steps) / ideal if ideal else None,
            "recipe": "batch_mesh_shapes(count=256, seed=2); mesh i perturbed +-0.05h with seed 1000+i"}
-    b.close()
     return out
 
 
@@ -571,7 +595,7 @@ def main():
     device = torch.device("cuda", dev)
     if args.batch:
         if rank == 0:
-            print(json.dumps(measure_batch(binding, args.steps, args.warmup, dev)), flush=True)
+            print(json.dumps(measure_batch(binding, args.steps, args.warmup, dev, alone=False)), flush=True)
         return
     if args.equation == "advection":
         if rank == 0:
