@@ -472,6 +472,27 @@ def measure_batch(binding, steps, warmup, dev, count=256, alone=True):
     ms = ev0.elapsed_time(ev1)
     _, rel = b.error()
     groups = b.groups()
+    single, per_stage = b.launch_mode()
+    # the other way of running a stage, timed the same way (one kernel for every degree
+    # group, or one launch per group on graph branches), where the batch offers it
+    other = None
+    try:
+        b.set_launch_mode(not single)
+    except binding.PyrDGError:
+        pass
+    else:
+        b.project(0.0)
+        for _ in range(warmup):
+            b.step(1, dt)
+        b.sync()
+        ev0.record(stream)
+        for _ in range(steps):
+            b.step(1, dt)
+        ev1.record(stream)
+        b.sync()
+        other = {"single_launch_per_stage": not single, "groups": b.groups(),
+                 "ms_per_step": ev0.elapsed_time(ev1) / steps}
+        b.set_launch_mode(single)
     b.close()
     # the same meshes one degree at a time: the sum of these step times is what the batch
     # would take if its degree groups ran one after another with no overlap and no tail
@@ -496,7 +517,9 @@ def measure_batch(binding, steps, warmup, dev, count=256, alone=True):
     ideal = sum(a["ms_per_step"] for a in alone_t) if alone_t else None
     out = {"meshes": count, "K_total": int(b.total_K), "dofs_total": int(b.total_dofs),
            "K_min": int(b.K.min()), "K_max": int(b.K.max()), "degrees": sorted(set(int(n) for n in b.N)),
-           "launches_per_stage": b.ngroups, "groups": groups, "precision": "f32", "steps": steps,
+           "single_launch_per_stage": single, "launches_per_stage": per_stage, "groups": groups,
+           "other_launch_mode": other,
+           "precision": "f32", "steps": steps,
            "ms_per_step": ms / steps, "dof_updates_per_s_per_stage": b.total_dofs * 5 * steps / (ms * 1e-3),
            "l2_rel_error_vs_exact_max": float(rel.max()),
            "degree_groups_alone": alone_t, "sum_of_groups_alone_ms_per_step": ideal,

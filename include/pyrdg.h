@@ -289,6 +289,17 @@ int pyr_dg_batch_group_info(const pyr_dg_batch* b, int group, int* N, int64_t* K
 int pyr_dg_batch_project(pyr_dg_batch* b, double t0);
 /* Per-mesh CFL time steps (as pyr_dg_dt_cfl) into dt[nmesh]. */
 int pyr_dg_batch_dt_cfl(const pyr_dg_batch* b, double cfl, double* dt);
+/* How the batch runs an RK stage (chosen at setup by timing both on the zero state):
+ * single_launch = 1: one persistent kernel per stage runs every degree group (FP32
+ * batches of 2..8 groups; the group's share of its CTAs is tuned from each group's
+ * measured cost), launches_per_stage = 1; single_launch = 0: one persistent launch per
+ * degree group, the groups on parallel branches of the step's CUDA graph,
+ * launches_per_stage = the group count. Either pointer may be NULL. */
+int pyr_dg_batch_launch_mode(const pyr_dg_batch* b, int* single_launch, int* launches_per_stage);
+/* Override that choice: single_launch != 0 selects the single kernel per stage
+ * (PYR_DG_ERR_BAD_ARG where it is not available), 0 the per-group launches. */
+int pyr_dg_batch_set_launch_mode(pyr_dg_batch* b, int single_launch);
+
 /* Advance every mesh nsteps LSRK4 steps of its own dt[i] > 0. Asynchronous. */
 int pyr_dg_batch_step(pyr_dg_batch* b, int nsteps, const double* dt);
 /* Per-mesh L2 errors (as pyr_dg_error) into l2_abs[nmesh], l2_rel[nmesh]

@@ -96,6 +96,8 @@ _SIGNATURES = {
     "pyr_dg_l2_diff": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_void_p, _c_dp, _c_dp]),
     "pyr_dg_host_nodal_points": (ctypes.c_int, [ctypes.c_int, _c_dp]),
     "pyr_dg_set_tensor_mixing": (ctypes.c_int, [_c_h, ctypes.c_int]),
+    "pyr_dg_batch_launch_mode": (ctypes.c_int, [_c_h, _c_ip, _c_ip]),
+    "pyr_dg_batch_set_launch_mode": (ctypes.c_int, [_c_h, ctypes.c_int]),
 }
 
 
@@ -401,6 +403,16 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+    def launch_mode(self):
+        """(single_launch, launches_per_stage): one kernel per stage for every degree group, or
+        one per group on parallel graph branches (chosen at setup by timing both)."""
+        a, n = ctypes.c_int(), ctypes.c_int()
+        _check(lib().pyr_dg_batch_launch_mode(self._h, ctypes.byref(a), ctypes.byref(n)))
+        return bool(a.value), n.value
+
+    def set_launch_mode(self, single_launch):
+        _check(lib().pyr_dg_batch_set_launch_mode(self._h, 1 if single_launch else 0))
 
     def groups(self):
         out = []

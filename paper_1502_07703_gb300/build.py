@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpyrdg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "batch.cu", "builder.cpp", "peak.cu"] + [f"inst_n{n}.cu" for n in range(1, 8)]
+SOURCES = ["api.cu", "batch.cu", "batch32.cu", "builder.cpp", "peak.cu"] + [f"inst_n{n}.cu" for n in range(1, 8)]
 
 
 def _nvcc():

@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(128, A32<N, EPB>::MIN_BLOCKS)
     decode_mode(n, k, j, i);
     s_dec[n] = k | j << 8 | i << 16;
   }
-  for (int x = tid; x < nrow * P3; x += S::NT) s_lx[x] = c32[C::LX + x];
-  for (int x = tid; x < nrow * n1; x += S::NT) s_dl[x] = c32[C::DL + x];
+  for (int x = tid; x < nrow * P3; x += S::NT) s_lx[x] = c32<N>[C::LX + x];
+  for (int x = tid; x < nrow * n1; x += S::NT) s_dl[x] = c32<N>[C::DL + x];
   // Y entries that no pass writes (face rows x face columns) stay zero
   for (int x = tid; x < EPB * n1 * nY; x += S::NT) s_Y0[x] = 0.f;
 
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(128, A32<N, EPB>::MIN_BLOCKS)
       const int64_t gl = elem(e0, ei) * Nfc + g;
       const float um = tr_cur[gl], up = tr_cur[mapP[gl]];
       const float* nv = face == 0 ? s_gf + 16 + 4 * idx : s_gf + 4 * (face - 1);
-      const float w = face == 0 ? c32[C::WB + idx] : c32[C::WFT + idx];
+      const float w = face == 0 ? c32<N>[C::WB + idx] : c32<N>[C::WFT + idx];
       const float bn = bx * nv[0] + by * nv[1] + bz * nv[2];
       s_Fs0[ei * Nfc + g] = w * nv[3] * 0.5f * (bn - alpha * fabsf(bn)) * (up - um);
     }
@@ -206,12 +206,12 @@ __global__ void __launch_bounds__(128, A32<N, EPB>::MIN_BLOCKS)
 #pragma unroll
           for (int k = 0; k <= N; ++k) {  // MG lower Hessenberg, MH tridiagonal
             if (k > kp + 1) continue;
-            ga = fmaf(c32[C::MG + kp * n1 + k], U0[k], ga);
+            ga = fmaf(c32<N>[C::MG + kp * n1 + k], U0[k], ga);
             if (k < kp - 1) continue;
-            al = fmaf(c32[C::MH + kp * n1 + k], Ua0[k], al);
-            be = fmaf(c32[C::MH + kp * n1 + k], Ub0[k], be);
+            al = fmaf(c32<N>[C::MH + kp * n1 + k], Ua0[k], al);
+            be = fmaf(c32<N>[C::MH + kp * n1 + k], Ub0[k], be);
           }
-          s_Y[kp * nY + p * YS + qq] = fmaf(c32[C::GB + kp], Fb, fmaf(b1, al, fmaf(b2, be, b3 * ga)));
+          s_Y[kp * nY + p * YS + qq] = fmaf(c32<N>[C::GB + kp], Fb, fmaf(b1, al, fmaf(b2, be, b3 * ga)));
         }
       }
     }
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(128, A32<N, EPB>::MIN_BLOCKS)
       for (int k = 0; k <= N; ++k) {
         float acc = 0.f;
 #pragma unroll
-        for (int m = 0; m <= N; ++m) acc = fmaf(c32[C::GF + k * n1 + m], Fm[m], acc);
+        for (int m = 0; m <= N; ++m) acc = fmaf(c32<N>[C::GF + k * n1 + m], Fm[m], acc);
         if (slot < 2)
           Yf[k * nY + ee * YS + n1 + slot] = acc;  // b = -1, +1 columns
         else
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(128, A32<N, EPB>::MIN_BLOCKS)
               if (c == j) acc = yv[c];
               continue;
             }
-            acc = fmaf(c32[C::LX + (tri_num(k) + j) * P3 + c], yv[c], acc);
+            acc = fmaf(c32<N>[C::LX + (tri_num(k) + j) * P3 + c], yv[c], acc);
           }
           s_Z[(tri_num(k) + j) * YS + pp] = acc;
         }
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(128, A32<N, EPB>::MIN_BLOCKS)
         for (int m = 0; m <= N; ++m) {
           float acc = 0.f;
 #pragma unroll
-          for (int k = 0; k <= N; ++k) acc = fmaf(c32[C::GF + k * n1 + m], Sk[k], acc);
+          for (int k = 0; k <= N; ++k) acc = fmaf(c32<N>[C::GF + k * n1 + m], Sk[k], acc);
           dst[face * n2 + t + n1 * m] = acc;
         }
       } else {  // base (c = -1) at (a_t, b_c) for every c
@@ -365,8 +365,8 @@ __global__ void __launch_bounds__(128, A32<N, EPB>::MIN_BLOCKS)
         for (int c = 0; c <= N; ++c) {
           float acc = 0.f;
 #pragma unroll
-          for (int rr = 0; rr < tri_num(N); ++rr) acc = fmaf(c32[C::CB + rr * n1 + c], at[rr], acc);
-          acc = fmaf(c32[C::GB + N], s_u[lvl_off(N) + c * n1 + t], acc);
+          for (int rr = 0; rr < tri_num(N); ++rr) acc = fmaf(c32<N>[C::CB + rr * n1 + c], at[rr], acc);
+          acc = fmaf(c32<N>[C::GB + N], s_u[lvl_off(N) + c * n1 + t], acc);
           dst[t + n1 * c] = acc;
         }
       }

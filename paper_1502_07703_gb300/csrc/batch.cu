@@ -23,6 +23,7 @@
 #include "../../include/pyrdg.h"
 #include "builder.h"
 #include "handle.h"
+#include "multi.h"
 
 using pyrdg::DeviceGuard;
 using pyrdg::fail;
@@ -45,6 +46,11 @@ struct pyr_dg_batch {
   int graph_nsteps = -1;
   std::vector<cudaStream_t> branch;  // one stream per degree group after the first (graph branches)
   std::vector<cudaEvent_t> branch_ev;  // fork event, then one join event per branch
+  // single-launch mode (FP32, 2..8 groups): one kernel per stage runs every group
+  bool multi = false;
+  size_t multi_smem = 0;
+  int multi_blocks = 0;
+  pyrdg::MultiArgs margs{};
 };
 
 namespace {
@@ -84,6 +90,155 @@ int time_grid(pyr_dg* h, int epb, int blocks, float* ms) {
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return fail(PYR_DG_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
   return rc;
+}
+
+// Traces of the current state into half 0 of every FP32 group's ping-pong pair, when any
+// group's are stale (after setup, projection or a state change); all groups then share the
+// current half.
+cudaError_t refresh_traces(pyr_dg_batch* b) {
+  bool stale = false;
+  for (pyr_dg* h : b->groups) stale = stale || (h->use_stage32 && !h->tr_valid);
+  if (!stale) return cudaSuccess;
+  for (pyr_dg* h : b->groups) {
+    if (!h->use_stage32) continue;
+    h->tr_cur = 0;
+    h->L->trace(h->K, h->q, h->tab, h->tr, b->stream);
+    h->tr_valid = true;
+  }
+  return cudaGetLastError();
+}
+
+// Enqueue nsteps steps of every mesh on the batch stream, starting from trace half `par`:
+// one single-launch kernel per stage (multi mode), or each degree group on its own branch
+// stream forked from and joined into the batch stream. Leaves the groups' host-side trace
+// half at `par` (the caller accounts for the flips).
+int enqueue_batch(pyr_dg_batch* b, int nsteps, int par, bool multi) {
+  if (multi) {
+    for (int n = 0; n < nsteps; ++n)
+      for (int st = 0; st < 5; ++st) {
+        pyrdg::multi_launch(b->margs, b->multi_blocks, b->multi_smem, (par + 5 * n + st) & 1, kRkA[st], kRkB[st],
+                            b->stream);
+      }
+    CUDA_TRY(cudaGetLastError());
+    return PYR_DG_OK;
+  }
+  int rc = PYR_DG_OK;
+  CUDA_TRY(cudaEventRecord(b->branch_ev[0], b->stream));
+  for (size_t g = 1; g < b->groups.size(); ++g) CUDA_TRY(cudaStreamWaitEvent(b->branch[g - 1], b->branch_ev[0], 0));
+  for (size_t g = 0; g < b->groups.size() && rc == PYR_DG_OK; ++g) {
+    pyr_dg* h = b->groups[g];
+    const cudaStream_t own = h->stream;
+    h->stream = g == 0 ? b->stream : b->branch[g - 1];
+    h->tr_cur = par;
+    rc = pyrdg::enqueue_steps(h, nsteps, 1.0);  // flips tr_cur on the host: restored below
+    h->stream = own;
+    h->tr_cur = par;
+    h->tr_valid = true;
+  }
+  for (size_t g = 1; g < b->groups.size(); ++g) {
+    CUDA_TRY(cudaEventRecord(b->branch_ev[g], b->branch[g - 1]));
+    CUDA_TRY(cudaStreamWaitEvent(b->stream, b->branch_ev[g], 0));
+  }
+  return rc;
+}
+
+// Time one enqueued step of the batch in the given mode (state and dt_elem zero: unchanged).
+int time_batch_step(pyr_dg_batch* b, bool multi, float* ms) {
+  CUDA_TRY(refresh_traces(b));
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(PYR_DG_ERR_CUDA, "autotune: cannot create an event");
+  }
+  int rc = enqueue_batch(b, 1, 0, multi);  // warm
+  if (rc == PYR_DG_OK) {
+    cudaEventRecord(e0, b->stream);
+    rc = enqueue_batch(b, 1, 1, multi);
+    cudaEventRecord(e1, b->stream);
+  }
+  const cudaError_t e = cudaEventSynchronize(e1);
+  if (rc == PYR_DG_OK && e == cudaSuccess) cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (pyr_dg* h : b->groups) h->tr_valid = false;
+  if (e != cudaSuccess) return fail(PYR_DG_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+  return rc;
+}
+
+// Single-launch mode for an FP32 batch of 2..8 degree groups: upload every degree's tables to
+// the multi-degree kernel, split its resident CTAs between the groups in proportion to each
+// group's measured cost (its step with all CTAs on that group alone), then keep the mode only
+// if a whole step is faster than the per-degree launches on graph branches.
+int tune_single_launch(pyr_dg_batch* b) {
+  const int ng = (int)b->groups.size();
+  if (ng < 2 || ng > pyrdg::kMaxMultiGroups) return PYR_DG_OK;
+  for (pyr_dg* h : b->groups)
+    if (!h->use_stage32) return PYR_DG_OK;
+  size_t smem = 0;
+  for (pyr_dg* h : b->groups) smem = std::max(smem, pyrdg::multi_smem(h->N));
+  for (pyr_dg* h : b->groups) {
+    pyrdg::RefTables T;
+    if (pyrdg::build_tables(h->N, T) != 0) return fail(PYR_DG_ERR_UNSUPPORTED_N, "table build failed");
+    CUDA_TRY(pyrdg::multi_prepare(h->N, T.tab.data(), smem));
+  }
+  int nsm = 1;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+  const int bps = pyrdg::multi_blocks_per_sm(smem);
+  if (bps <= 0) return PYR_DG_OK;
+  const int total = bps * nsm;
+  b->multi_smem = smem;
+  pyrdg::MultiArgs all{};
+  all.ngroups = ng;
+  std::vector<int64_t> egroups(ng);
+  for (int g = 0; g < ng; ++g) {
+    pyr_dg* h = b->groups[g];
+    pyrdg::MultiGroup& G = all.g[g];
+    G.N = h->N;
+    G.bc = h->bc;
+    G.tau = (float)h->tau;
+    G.K = h->K;
+    G.q = (float*)h->q;
+    G.res = (float*)h->res;
+    G.tr[0] = (float*)h->tr;
+    G.tr[1] = (float*)h->tr2;
+    G.mapP = h->mapP;
+    G.geo = (const float*)h->geo;
+    G.gface = (const float*)h->gface;
+    G.invM = (const float*)h->invM;
+    G.dt_elem = (const float*)h->dt_elem;
+    const int epb = pyrdg::multi_epb_of(h->N);
+    egroups[g] = (h->K + epb - 1) / epb;
+  }
+  // cost of each group: all CTAs (up to its element groups) on it alone
+  std::vector<float> cost(ng, 0.f);
+  float sum = 0.f;
+  for (int g = 0; g < ng; ++g) {
+    b->margs.ngroups = 1;
+    b->margs.g[0] = all.g[g];
+    b->margs.g[0].blk0 = 0;
+    b->margs.g[0].nblk = (int)std::min<int64_t>(total, egroups[g]);
+    b->multi_blocks = b->margs.g[0].nblk;
+    const int rc = time_batch_step(b, true, &cost[g]);
+    if (rc != PYR_DG_OK) return rc;
+    sum += cost[g];
+  }
+  // split: proportional to cost, at least one CTA each, never more than a group's element groups
+  int blk0 = 0;
+  for (int g = 0; g < ng; ++g) {
+    const int64_t share = (int64_t)std::llround((double)cost[g] / sum * total);
+    all.g[g].blk0 = blk0;
+    all.g[g].nblk = (int)std::max<int64_t>(1, std::min<int64_t>(egroups[g], share));
+    blk0 += all.g[g].nblk;
+  }
+  b->margs = all;
+  b->multi_blocks = blk0;
+  float t_multi = 0.f, t_branch = 0.f;
+  int rc = time_batch_step(b, true, &t_multi);
+  if (rc == PYR_DG_OK) rc = time_batch_step(b, false, &t_branch);
+  if (rc != PYR_DG_OK) return rc;
+  b->multi = t_multi < t_branch;
+  return PYR_DG_OK;
 }
 
 }  // namespace
@@ -241,6 +396,13 @@ int pyr_dg_batch_setup(int nmesh, const double* const* vertices, const int64_t* 
     }
     b->branch_ev.push_back(ev);
   }
+  {
+    const int trc = tune_single_launch(b);
+    if (trc != PYR_DG_OK) {
+      destroy_batch(b);
+      return trc;
+    }
+  }
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
     destroy_batch(b);
     return fail(PYR_DG_ERR_CUDA, "batch setup failed");
@@ -269,8 +431,39 @@ int pyr_dg_batch_group_info(const pyr_dg_batch* b, int group, int* N, int64_t* K
   const pyr_dg* h = b->groups[group];
   if (N) *N = h->N;
   if (K) *K = h->K;
+  if (b->multi) {  // the group's CTAs of the single-launch kernel
+    if (stage_blocks) *stage_blocks = b->margs.g[group].nblk;
+    if (elems_per_block) *elems_per_block = pyrdg::multi_epb_of(h->N);
+    return PYR_DG_OK;
+  }
   if (stage_blocks) *stage_blocks = h->use_stage32 ? h->stage_blocks : (int)h->K;
   if (elems_per_block) *elems_per_block = h->use_stage32 ? h->stage_epb : 1;
+  return PYR_DG_OK;
+}
+
+int pyr_dg_batch_set_launch_mode(pyr_dg_batch* b, int single_launch) {
+  if (!b) return fail(PYR_DG_ERR_BAD_ARG, "null batch");
+  if (single_launch && b->multi_blocks <= 0)
+    return fail(PYR_DG_ERR_BAD_ARG, "the single-launch stage needs an FP32 batch of 2 to %d degree groups",
+                pyrdg::kMaxMultiGroups);
+  if ((single_launch != 0) != b->multi) {
+    DeviceGuard g(b->device);
+    CUDA_TRY(g.err);
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    for (cudaGraphExec_t& gx : b->graph)
+      if (gx) {
+        cudaGraphExecDestroy(gx);
+        gx = nullptr;
+      }
+    b->multi = single_launch != 0;
+  }
+  return PYR_DG_OK;
+}
+
+int pyr_dg_batch_launch_mode(const pyr_dg_batch* b, int* single_launch, int* launches_per_stage) {
+  if (!b) return fail(PYR_DG_ERR_BAD_ARG, "null batch");
+  if (single_launch) *single_launch = b->multi ? 1 : 0;
+  if (launches_per_stage) *launches_per_stage = b->multi ? 1 : (int)b->groups.size();
   return PYR_DG_OK;
 }
 
@@ -335,48 +528,19 @@ int pyr_dg_batch_step(pyr_dg_batch* b, int nsteps, const double* dt) {
       }
     b->graph_nsteps = nsteps;
   }
-  // FP32 groups: traces of the current state in half 0 of the ping-pong pair when any group's
-  // are stale (after setup, projection or a state change); all groups then share the half
-  bool stale = false;
-  for (pyr_dg* h : b->groups) stale = stale || (h->use_stage32 && !h->tr_valid);
-  if (stale) {
-    for (pyr_dg* h : b->groups) {
-      if (!h->use_stage32) continue;
-      h->tr_cur = 0;
-      h->L->trace(h->K, h->q, h->tab, h->tr, b->stream);
-      h->tr_valid = true;
-    }
-    CUDA_TRY(cudaGetLastError());
-  }
+  CUDA_TRY(refresh_traces(b));
   int par = 0;
   for (pyr_dg* h : b->groups)
     if (h->use_stage32) par = h->tr_cur;
   if (!b->graph[par]) {
-    // group 0 on the batch stream, group g > 0 on branch g-1, forked from and joined into it
     cudaGraph_t graph = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = PYR_DG_OK;
-    cudaError_t ce = cudaEventRecord(b->branch_ev[0], b->stream);
-    for (size_t g = 1; g < b->groups.size() && ce == cudaSuccess; ++g)
-      ce = cudaStreamWaitEvent(b->branch[g - 1], b->branch_ev[0], 0);
-    for (size_t g = 0; g < b->groups.size() && ce == cudaSuccess && rc == PYR_DG_OK; ++g) {
-      pyr_dg* h = b->groups[g];
-      const cudaStream_t own = h->stream;
-      h->stream = g == 0 ? b->stream : b->branch[g - 1];
-      rc = pyrdg::enqueue_steps(h, nsteps, 1.0);  // flips tr_cur on the host: restored below
-      h->stream = own;
-      h->tr_cur = par;
-      h->tr_valid = true;
-    }
-    for (size_t g = 1; g < b->groups.size() && ce == cudaSuccess; ++g) {
-      ce = cudaEventRecord(b->branch_ev[g], b->branch[g - 1]);
-      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->stream, b->branch_ev[g], 0);
-    }
+    const int rc = enqueue_batch(b, nsteps, par, b->multi);
     const cudaError_t ee = cudaStreamEndCapture(b->stream, &graph);
-    if (rc != PYR_DG_OK || ce != cudaSuccess || ee != cudaSuccess) {
+    if (rc != PYR_DG_OK || ee != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
       if (rc != PYR_DG_OK) return rc;
-      return fail(PYR_DG_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+      return fail(PYR_DG_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ee));
     }
     const cudaError_t ie = cudaGraphInstantiate(&b->graph[par], graph, 0);
     cudaGraphDestroy(graph);

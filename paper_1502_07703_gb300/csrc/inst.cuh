@@ -294,25 +294,7 @@ struct Impl {
     return 0;
   }
   static cudaError_t upload_c32(const double* tab) {
-    using C = C32<N>;
-    constexpr TabLayout L(N);
-    static_assert(C::size <= C32<7>::size, "constant table size");
-    float h[C::size];
-    for (int x = 0; x < d::nrow * d::P3; ++x) h[C::LX + x] = (float)tab[L.LX + x];
-    for (int x = 0; x < d::nrow * d::n1; ++x) h[C::DL + x] = (float)tab[L.DL + x];
-    for (int x = 0; x < d::n2; ++x) {
-      h[C::MH + x] = (float)tab[L.MH + x];
-      h[C::MG + x] = (float)tab[L.MG + x];
-      h[C::GF + x] = (float)tab[L.GF + x];
-      h[C::WB + x] = (float)tab[L.WB + x];
-      h[C::WFT + x] = (float)tab[L.WFT + x];
-    }
-    for (int k = 0; k <= N; ++k) h[C::GB + k] = (float)tab[L.GB + k];
-    for (int k = 0; k <= N; ++k)
-      for (int j = 0; j <= k; ++j)
-        for (int c = 0; c <= N; ++c)
-          h[C::CB + (tri_num(k) + j) * d::n1 + c] = (float)(tab[L.GB + k] * tab[L.LX + (tri_num(k) + j) * d::P3 + c]);
-    cudaError_t e = cudaMemcpyToSymbol(c32, h, sizeof(float) * C::size);
+    cudaError_t e = upload_c32_tables<N>(tab);
     if (e == cudaSuccess) e = smem32<1>();
     if (e == cudaSuccess) e = smem32<2>();
     if (e == cudaSuccess) e = smem32<4>();

@@ -39,9 +39,36 @@ struct C32 {
   static constexpr int size = CB + d::nrow * d::n1;
 };
 
-// One copy per translation unit (each unit instantiates one degree); filled by
-// upload_c32() from the double tables, rounded to float.
-static __constant__ float c32[C32<7>::size];
+// One copy per translation unit and degree; filled by upload_c32_tables<N>() from the double
+// tables, rounded to float.
+template <int N>
+static __constant__ float c32[C32<N>::size];
+
+// Fill this translation unit's constant table of degree N from the double tables (TabLayout).
+// Internal linkage like the table itself: an instantiation shared between units (the default
+// for function templates) could upload into another unit's copy.
+template <int N>
+static cudaError_t upload_c32_tables(const double* tab) {
+  using C = C32<N>;
+  using d = Dims<N>;
+  constexpr TabLayout L(N);
+  float h[C::size];
+  for (int x = 0; x < d::nrow * d::P3; ++x) h[C::LX + x] = (float)tab[L.LX + x];
+  for (int x = 0; x < d::nrow * d::n1; ++x) h[C::DL + x] = (float)tab[L.DL + x];
+  for (int x = 0; x < d::n2; ++x) {
+    h[C::MH + x] = (float)tab[L.MH + x];
+    h[C::MG + x] = (float)tab[L.MG + x];
+    h[C::GF + x] = (float)tab[L.GF + x];
+    h[C::WB + x] = (float)tab[L.WB + x];
+    h[C::WFT + x] = (float)tab[L.WFT + x];
+  }
+  for (int k = 0; k <= N; ++k) h[C::GB + k] = (float)tab[L.GB + k];
+  for (int k = 0; k <= N; ++k)
+    for (int j = 0; j <= k; ++j)
+      for (int c = 0; c <= N; ++c)
+        h[C::CB + (tri_num(k) + j) * d::n1 + c] = (float)(tab[L.GB + k] * tab[L.LX + (tri_num(k) + j) * d::P3 + c]);
+  return cudaMemcpyToSymbol(c32<N>, h, sizeof(float) * C::size);
+}
 
 // Ask L2 to fetch the 128-byte lines of [p, p + bytes) (one line per participating thread).
 __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, int tid, int nthr) {
@@ -227,12 +254,16 @@ constexpr int kTcWaitPolls = 1 << 20;
 // Timeouts of the tensor-core mixing's waits since the host last read and cleared them.
 static __device__ int g_tc32_timeouts;
 
+// One RK stage of a mesh by CTA blk of nblk persistent CTAs (grid-stride over element groups):
+// the body of stage32_kernel, also run per degree group by the batch's single-launch kernel.
 template <int N, int EPB, bool TC = false>
-__global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
-    stage32_kernel(int64_t K, float* __restrict__ q, float* __restrict__ res, const float* __restrict__ tr_cur,
-                    float* __restrict__ tr_nxt, const int32_t* __restrict__ mapP, const float* __restrict__ geo,
-                    const float* __restrict__ gface, const float* __restrict__ invM, int bc, float tau, float rka,
-                    float rkb, float dt, const float* __restrict__ dt_elem, int write_traces) {
+__device__ __forceinline__ void stage32_run(int64_t K, float* __restrict__ q, float* __restrict__ res,
+                                            const float* __restrict__ tr_cur, float* __restrict__ tr_nxt,
+                                            const int32_t* __restrict__ mapP, const float* __restrict__ geo,
+                                            const float* __restrict__ gface, const float* __restrict__ invM, int bc,
+                                            float tau, float rka, float rkb, float dt,
+                                            const float* __restrict__ dt_elem, int write_traces, int64_t blk,
+                                            int64_t nblk) {
   using d = Dims<N>;
   using S = S32<N, EPB, TC>;
   using C = C32<N>;
@@ -252,8 +283,8 @@ __global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
     decode_mode(n, k, j, i);
     s_dec[n] = k | j << 8 | i << 16;
   }
-  for (int x = tid; x < nrow * P3; x += S::NT) s_lx[x] = c32[C::LX + x];
-  for (int x = tid; x < nrow * n1; x += S::NT) s_dl[x] = c32[C::DL + x];
+  for (int x = tid; x < nrow * P3; x += S::NT) s_lx[x] = c32<N>[C::LX + x];
+  for (int x = tid; x < nrow * n1; x += S::NT) s_dl[x] = c32<N>[C::DL + x];
   // Y entries that no pass writes (face rows x face columns) stay zero
   for (int x = tid; x < EPB * 4 * n1 * nY; x += S::NT) s_Y0[x] = 0.f;
   // tensor-core mixing: B tiles (TF32 hi and lo parts of the mixing matrices), the mbarrier
@@ -269,11 +300,11 @@ __global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
       const int n = x / KT, k = x - n * KT;
       float v = 0.f;
       const int kp = n % n1, kk = k % n1;  // output level k', input level k
-      if (n < n1 && k < n1) v = c32[C::MG + kp * n1 + kk];                          // Y_p <- Zc (c derivative)
-      else if (n < n1 && k < 2 * n1) v = c32[C::MH + kp * n1 + kk];                 // Y_p <- X (r, s derivatives)
-      else if (n >= n1 && n < 2 * n1 && k >= 2 * n1 && k < 3 * n1) v = c32[C::MG + kp * n1 + kk];  // G <- U
-      else if (n >= 2 * n1 && n < 3 * n1 && k >= 3 * n1 && k < 4 * n1) v = c32[C::MH + kp * n1 + kk];  // alpha <- U_a
-      else if (n >= 3 * n1 && n < 4 * n1 && k >= 4 * n1 && k < 5 * n1) v = c32[C::MH + kp * n1 + kk];  // beta <- U_b
+      if (n < n1 && k < n1) v = c32<N>[C::MG + kp * n1 + kk];                          // Y_p <- Zc (c derivative)
+      else if (n < n1 && k < 2 * n1) v = c32<N>[C::MH + kp * n1 + kk];                 // Y_p <- X (r, s derivatives)
+      else if (n >= n1 && n < 2 * n1 && k >= 2 * n1 && k < 3 * n1) v = c32<N>[C::MG + kp * n1 + kk];  // G <- U
+      else if (n >= 2 * n1 && n < 3 * n1 && k >= 3 * n1 && k < 4 * n1) v = c32<N>[C::MH + kp * n1 + kk];  // alpha <- U_a
+      else if (n >= 3 * n1 && n < 4 * n1 && k >= 4 * n1 && k < 5 * n1) v = c32<N>[C::MH + kp * n1 + kk];  // beta <- U_b
       float hi, lo;
       tf32_split(v, hi, lo);
       Bh[tc_offset<KT>(n, k)] = hi;
@@ -319,10 +350,10 @@ __global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
     }
     cp_async_commit();
   };
-  const int64_t gstride = (int64_t)gridDim.x * EPB;
-  if ((int64_t)blockIdx.x * EPB < K) issue((int64_t)blockIdx.x * EPB, sm + S::buf);
+  const int64_t gstride = nblk * EPB;
+  if (blk * EPB < K) issue(blk * EPB, sm + S::buf);
   int it = 0;
-  for (int64_t e0 = (int64_t)blockIdx.x * EPB; e0 < K; e0 += gstride, ++it) {
+  for (int64_t e0 = blk * EPB; e0 < K; e0 += gstride, ++it) {
     const int ne = EPB == 1 ? 1 : (int)min((int64_t)EPB, K - e0);  // elements of the group in the mesh
     float* bcur = sm + S::buf + (it & 1) * EPB * S::bsz;
     cp_async_wait_all();  // this thread's copies of the group have landed
@@ -346,7 +377,7 @@ __global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
       const float um[4] = {a4.x, a4.y, a4.z, a4.w};
       const float up[4] = {b4.x, b4.y, b4.z, b4.w};
       const float* nv = face == 0 ? s_gf + 16 + 4 * idx : s_gf + 4 * (face - 1);
-      const float w = face == 0 ? c32[C::WB + idx] : c32[C::WFT + idx];
+      const float w = face == 0 ? c32<N>[C::WB + idx] : c32<N>[C::WFT + idx];
       float F[4];
       face_flux<float>(um, up, gn == gl, bc, tau, nv, w * nv[3], F);
       float* s_Fs = s_Fs0 + ei * 4 * Nfc;
@@ -499,7 +530,7 @@ __global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
         if (half == 0) {
           const float Fb = s_Fs0[pq];
 #pragma unroll
-          for (int kp = 0; kp <= N; ++kp) s_Y0[kp * nY + p * YS + qq] = fmaf(c32[C::GB + kp], Fb, acc[kp]);
+          for (int kp = 0; kp <= N; ++kp) s_Y0[kp * nY + p * YS + qq] = fmaf(c32<N>[C::GB + kp], Fb, acc[kp]);
         } else {
           float Fb[3];
 #pragma unroll
@@ -507,7 +538,7 @@ __global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
 #pragma unroll
           for (int kp = 0; kp <= N; ++kp) {
             const float ga = acc[kp], al = acc[n1 + kp], be = acc[2 * n1 + kp];
-            const float gb = c32[C::GB + kp];
+            const float gb = c32<N>[C::GB + kp];
             const int yo = kp * nY + p * YS + qq;
 #pragma unroll
             for (int m = 0; m < 3; ++m)
@@ -543,10 +574,10 @@ __global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
 #pragma unroll
               for (int k = 0; k <= N; ++k) {  // MG lower Hessenberg, MH tridiagonal
                 if (k > kp + 1) continue;
-                dv = fmaf(c32[C::MG + kp * n1 + k], Zc[k], dv);
-                if (k >= kp - 1) dv = fmaf(c32[C::MH + kp * n1 + k], X[k], dv);
+                dv = fmaf(c32<N>[C::MG + kp * n1 + k], Zc[k], dv);
+                if (k >= kp - 1) dv = fmaf(c32<N>[C::MH + kp * n1 + k], X[k], dv);
               }
-              s_Y[kp * nY + p * YS + qq] = fmaf(c32[C::GB + kp], Fb, dv);
+              s_Y[kp * nY + p * YS + qq] = fmaf(c32<N>[C::GB + kp], Fb, dv);
             }
           } else {
             float U0[n1], Ua0[n1], Ub0[n1];
@@ -560,12 +591,12 @@ __global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
 #pragma unroll
               for (int k = 0; k <= N; ++k) {  // MG lower Hessenberg, MH tridiagonal
                 if (k > kp + 1) continue;
-                ga = fmaf(c32[C::MG + kp * n1 + k], U0[k], ga);
+                ga = fmaf(c32<N>[C::MG + kp * n1 + k], U0[k], ga);
                 if (k < kp - 1) continue;
-                al = fmaf(c32[C::MH + kp * n1 + k], Ua0[k], al);
-                be = fmaf(c32[C::MH + kp * n1 + k], Ub0[k], be);
+                al = fmaf(c32<N>[C::MH + kp * n1 + k], Ua0[k], al);
+                be = fmaf(c32<N>[C::MH + kp * n1 + k], Ub0[k], be);
               }
-              const float gb = c32[C::GB + kp];
+              const float gb = c32<N>[C::GB + kp];
               const int yo = kp * nY + p * YS + qq;
 #pragma unroll
               for (int m = 0; m < 3; ++m)
@@ -590,7 +621,7 @@ __global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
       for (int k = 0; k <= N; ++k) {
         float acc = 0.f;
 #pragma unroll
-        for (int m = 0; m <= N; ++m) acc = fmaf(c32[C::GF + k * n1 + m], Fm[m], acc);
+        for (int m = 0; m <= N; ++m) acc = fmaf(c32<N>[C::GF + k * n1 + m], Fm[m], acc);
         if (slot < 2)
           Yf[k * nY + ee * YS + n1 + slot] = acc;  // b = -1, +1 columns
         else
@@ -623,7 +654,7 @@ __global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
               if (c == j) acc = yv[c];
               continue;
             }
-            acc = fmaf(c32[C::LX + (tri_num(k) + j) * P3 + c], yv[c], acc);
+            acc = fmaf(c32<N>[C::LX + (tri_num(k) + j) * P3 + c], yv[c], acc);
           }
           s_Z[(f * nrow + tri_num(k) + j) * YS + pp] = acc;
         }
@@ -726,7 +757,7 @@ __global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
         for (int m = 0; m <= N; ++m) {
           float acc = 0.f;
 #pragma unroll
-          for (int k = 0; k <= N; ++k) acc = fmaf(c32[C::GF + k * n1 + m], Sk[k], acc);
+          for (int k = 0; k <= N; ++k) acc = fmaf(c32<N>[C::GF + k * n1 + m], Sk[k], acc);
           dst[4 * (face * n2 + t + n1 * m) + f] = acc;
         }
       } else {  // base (c = -1) at (a_t, b_c) for every c
@@ -740,9 +771,9 @@ __global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
         for (int c = 0; c <= N; ++c) {
           float acc = 0.f;
 #pragma unroll
-          for (int rr = 0; rr < tri_num(N); ++rr) acc = fmaf(c32[C::CB + rr * n1 + c], at[rr], acc);
+          for (int rr = 0; rr < tri_num(N); ++rr) acc = fmaf(c32<N>[C::CB + rr * n1 + c], at[rr], acc);
           // level N: l_j^N(b_c) = delta_jc and At[N][t < n1] is u
-          acc = fmaf(c32[C::GB + N], s_u[f * Np + lvl_off(N) + c * n1 + t], acc);
+          acc = fmaf(c32<N>[C::GB + N], s_u[f * Np + lvl_off(N) + c * n1 + t], acc);
           dst[4 * (t + n1 * c) + f] = acc;
         }
       }
@@ -759,6 +790,16 @@ __global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
     __syncthreads();
     if (tid < 32) tc_dealloc(tmem, 32);
   }
+}
+
+template <int N, int EPB, bool TC = false>
+__global__ void __launch_bounds__(128, S32<N, EPB, TC>::MIN_BLOCKS)
+    stage32_kernel(int64_t K, float* __restrict__ q, float* __restrict__ res, const float* __restrict__ tr_cur,
+                   float* __restrict__ tr_nxt, const int32_t* __restrict__ mapP, const float* __restrict__ geo,
+                   const float* __restrict__ gface, const float* __restrict__ invM, int bc, float tau, float rka,
+                   float rkb, float dt, const float* __restrict__ dt_elem, int write_traces) {
+  stage32_run<N, EPB, TC>(K, q, res, tr_cur, tr_nxt, mapP, geo, gface, invM, bc, tau, rka, rkb, dt, dt_elem,
+                          write_traces, blockIdx.x, gridDim.x);
 }
 
 }  // namespace pyrdg

@@ -175,3 +175,46 @@ def test_batch_replays_alternate_trace_halves(torch_cuda):
         for got, want in ((mid[i], U5), (end[i], U4)):
             rel = np.linalg.norm(got - want) / np.linalg.norm(want)
             assert rel <= 1e-6, (i, rel)
+
+
+@pytest.mark.parametrize("single", [True, False])
+def test_batch_launch_modes_against_single_meshes_and_oracle(torch_cuda, single):
+    """Both ways of running an FP32 batch stage: one kernel for every degree group (CTAs
+    split between the groups) and one launch per group on graph branches. Steps, replays and a
+    projection against single-mesh runs (1e-6) and one mesh per degree against the oracle."""
+    from paper_1502_07703_gb300.binding import Batch, Solver
+    meshes = _meshes()
+    with Batch(meshes, precision="f32") as b:
+        b.set_launch_mode(single)
+        assert b.launch_mode() == (single, 1 if single else b.ngroups)
+        dt = b.dt_cfl(0.5)
+        b.project(0.0)
+        b.step(2, dt)
+        b.step(1, dt)
+        b.step(1, dt)
+        states = [b.get_state(i).astype(np.float64) for i in range(b.nmesh)]
+    seen = set()
+    for i, (v, e, n) in enumerate(meshes):
+        with Solver(v, e, n, precision="f32") as s:
+            s.project(0.0)
+            s.step(4, dt[i])
+            U = s.get_state().astype(np.float64)
+        rel = np.linalg.norm(states[i] - U) / np.linalg.norm(U)
+        assert rel <= 1e-6, (i, rel)
+        if n not in seen:
+            seen.add(n)
+            dg = PyramidDG(v, e, n)
+            check(dg, dg.values_phi(states[i]), dg.values_psi(dg.lsrk4(dg.project_exact(0.0), dt[i], 4)), 1e-5,
+                  (single, n))
+
+
+def test_batch_single_launch_refused_where_unavailable(torch_cuda):
+    from paper_1502_07703_gb300.binding import Batch, PyrDGError
+    v, e = make_pyramid_mesh(1, delta=0.05, seed=3)
+    with Batch([(v, e, 2), (v, e, 3)], precision="f64") as b:
+        with pytest.raises(PyrDGError, match="BAD_ARG"):
+            b.set_launch_mode(True)
+        b.set_launch_mode(False)
+    with Batch([(v, e, 2), (v, e, 2)], precision="f32") as b:  # one degree group
+        with pytest.raises(PyrDGError, match="BAD_ARG"):
+            b.set_launch_mode(True)
