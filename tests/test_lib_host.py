@@ -146,3 +146,31 @@ def test_setup_rejects_empty_and_degenerate_meshes():
     bad[0, 2] = v.shape[0]                         # vertex index out of range
     with pytest.raises(binding.PyrDGError, match="BAD"):
         binding.Solver(v, bad, 2)
+
+
+def test_newer_calls_check_their_arguments_on_the_host():
+    """Null handles and out-of-range arguments of the nodal, tensor-core, L2-distance and batch
+    launch-mode calls are refused before any device work."""
+    L = binding.lib()
+    assert L.pyr_dg_l2_diff(None, None, None, None, None) == -1
+    assert L.pyr_dg_set_tensor_mixing(None, 1) == -1
+    assert L.pyr_dg_batch_launch_mode(None, None, None) == -1
+    assert L.pyr_dg_batch_set_launch_mode(None, 1) == -1
+    x = np.empty(3 * 100)
+    assert L.pyr_dg_host_nodal_points(0, x.ctypes.data_as(binding._c_dp)) == -3
+    assert L.pyr_dg_host_nodal_points(8, x.ctypes.data_as(binding._c_dp)) == -3
+    assert L.pyr_dg_host_nodal_points(3, None) == -1
+    v, e = make_pyramid_mesh(1)
+    for kw in ({"precision": "f32"}, {"equation": "advection", "periodic": (0.0, 1.0)}):
+        with pytest.raises(binding.PyrDGError, match="BAD_ARG"):
+            binding.Solver(v, e, 2, basis="nodal", **kw)
+    o = binding.Opts()
+    L.pyr_dg_default_opts(ctypes.byref(o))
+    assert o.basis == binding.PYR_DG_MODAL
+    o.basis = 7
+    V = np.ascontiguousarray(v, dtype=np.float64)
+    E = np.ascontiguousarray(e, dtype=np.int32)
+    h = ctypes.c_void_p()
+    assert L.pyr_dg_setup(V.ctypes.data_as(binding._c_dp), V.shape[0], E.ctypes.data_as(binding._c_i32p),
+                          E.shape[0], 2, ctypes.byref(o), ctypes.byref(h)) == -1
+    assert b"basis" in L.pyr_dg_last_error()
