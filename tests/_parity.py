@@ -39,3 +39,35 @@ def record(rel, worst, tol, ctx=None):
                                  "ctx": repr(ctx), "rel_l2": float(rel), "worst_element": float(worst),
                                  "tol": tol}) + "\n")
     assert rel <= tol and worst <= tol, (ctx, "rel", rel, "worst element", worst, "tol", tol)
+
+
+def face_neighbours(EToV):
+    """Element adjacency through shared faces (test-side, from vertex sets only)."""
+    faces = ((0, 1, 2, 3), (0, 1, 4), (1, 2, 4), (3, 2, 4), (0, 3, 4))
+    owner = {}
+    nbrs = [[] for _ in range(len(EToV))]
+    for k, row in enumerate(EToV):
+        for f in faces:
+            key = tuple(sorted(int(row[i]) for i in f))
+            if key in owner:
+                j = owner.pop(key)
+                nbrs[k].append(j)
+                nbrs[j].append(k)
+            else:
+                owner[key] = k
+    return nbrs
+
+
+def patch(nbrs, centre, radius):
+    """Sorted element indices within `radius` face hops of `centre`."""
+    seen = {centre: 0}
+    frontier = [centre]
+    for r in range(radius):
+        nxt = []
+        for k in frontier:
+            for j in nbrs[k]:
+                if j not in seen:
+                    seen[j] = r + 1
+                    nxt.append(j)
+        frontier = nxt
+    return sorted(seen)

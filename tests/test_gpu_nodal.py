@@ -103,3 +103,27 @@ def test_nodal_state_roundtrip_and_rejections(torch_cuda):
     for kw in ({"precision": "f32"}, {"equation": "advection", "periodic": (0.0, 1.0)}):
         with pytest.raises(PyrDGError, match="BAD_ARG"):
             Solver(v, e, 2, basis="nodal", **kw)
+
+
+def test_nodal_full_size_sampled(torch_cuda):
+    """The bench's mesh (32^3 hexes x 6 = 196,608 pyramids, +-0.05h, seed 1) at N = 4 in the
+    nodal basis: one LSRK4 step from the projected standing wave, checked on sampled elements
+    whose 6-hop neighbourhood the oracle advances (influence crosses one face per stage)."""
+    from _parity import face_neighbours, patch as _patch
+    v, e = make_pyramid_mesh(32, delta=0.05, seed=1)
+    K, N = e.shape[0], 4
+    nbrs = face_neighbours(e)
+    rng = np.random.default_rng(23)
+    samples = [int(x) for x in rng.choice(K, 2, replace=False)] + [K - 1]
+    dt = PyramidDG(v, e[:6], N).dt_cfl(0.5)
+    with _solver(v, e, N) as s:
+        s.project(0.0)
+        s.step(1, dt)
+        U1 = s.get_state()
+    for c in samples:
+        patch = _patch(nbrs, c, 6)
+        dg = PyramidDG(v, e[patch], N)
+        i = patch.index(c)
+        Up = dg.lsrk4(dg.project_exact(0.0), dt, 1)
+        check(dg, dg.values_psi(psi_from_nodal(N, U1[patch]))[i:i + 1], dg.values_psi(Up)[i:i + 1], TOL["f64"], c,
+              elems=[i])

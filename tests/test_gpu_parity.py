@@ -12,7 +12,7 @@ the target states).
 import numpy as np
 import pytest
 
-from _parity import TOL, check, record
+from _parity import TOL, check, face_neighbours as _face_neighbours, patch as _patch, record
 from oracle.dg import PyramidDG
 from paper_1502_07703_gb300.mesh import make_pyramid_mesh, random_state
 
@@ -184,37 +184,6 @@ def test_state_roundtrip_host_and_device(torch_cuda):
             s.set_state(d * 2, t=0.0)
             np.testing.assert_array_equal(s.get_state(), 2 * U)
             np.testing.assert_array_equal(d.cpu().numpy(), U)
-
-
-def _face_neighbours(EToV):
-    """Element adjacency through shared faces (test-side, from vertex sets only)."""
-    faces = ((0, 1, 2, 3), (0, 1, 4), (1, 2, 4), (3, 2, 4), (0, 3, 4))
-    owner = {}
-    nbrs = [[] for _ in range(len(EToV))]
-    for k, row in enumerate(EToV):
-        for f in faces:
-            key = tuple(sorted(int(row[i]) for i in f))
-            if key in owner:
-                j = owner.pop(key)
-                nbrs[k].append(j)
-                nbrs[j].append(k)
-            else:
-                owner[key] = k
-    return nbrs
-
-
-def _patch(nbrs, centre, radius):
-    seen = {centre: 0}
-    frontier = [centre]
-    for r in range(radius):
-        nxt = []
-        for k in frontier:
-            for j in nbrs[k]:
-                if j not in seen:
-                    seen[j] = r + 1
-                    nxt.append(j)
-        frontier = nxt
-    return sorted(seen)
 
 
 def test_full_size_config2_sampled(torch_cuda):
