@@ -97,6 +97,14 @@ def stage_bytes_per_element(n, tb):
     return tb * (4 * 4 * Np + 3 * 4 * Nfc + 9 * n2 + 16 + 4 * n2 + Np) + 4 * Nfc
 
 
+def nodal_extra_flops_per_element(n):
+    """Flops the nodal variant adds to the modal stage per element: the dense changes of basis
+    V^{-1} u, V^T s and V r (4 fields, Np^2 multiply-adds each) and the triangle faces' nodal
+    mass matrices (4 faces x 4 fields x nT^2)."""
+    Np, nT = num_modes(n), (n + 1) * (n + 2) // 2
+    return 2 * (3 * 4 * Np * Np + 16 * nT * nT)
+
+
 def trace_flops_per_element(n):
     """Algorithmic flops of the trace interpolation of one element's state (Alg. 3):
     a pass at the N+3 a points (the level-N volume columns are the coefficients
@@ -590,6 +598,8 @@ def main():
     ap.add_argument("--degree", type=int, default=N, help="polynomial degree (4 = the benchmark workload)")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"],
                     help="f64 = the benchmark workload; f32 = the precision form (for profiling runs)")
+    ap.add_argument("--basis", default="modal", choices=["modal", "nodal"],
+                    help="with --precision f64: the nodal variant (Sec. 4.4.1) for profiling runs")
     ap.add_argument("--tensor-mixing", action="store_true",
                     help="with --precision f32: the stage kernel with the level mixing on the tensor cores "
                          "(for profiling runs)")
@@ -631,7 +641,7 @@ def main():
         return
     v, e = make_pyramid_mesh(args.nx, delta=DELTA, seed=SEED)
     nd, prec = args.degree, args.precision
-    s = binding.Solver(v, e, nd, precision=prec, bc="wall", tau=1.0, device=dev)
+    s = binding.Solver(v, e, nd, precision=prec, bc="wall", tau=1.0, device=dev, basis=args.basis)
     if args.tensor_mixing:
         s.set_tensor_mixing(True)
     K, Np = s.K, s.Np
@@ -671,8 +681,12 @@ def main():
     rhs_avg_s = rhs_ms / rhs_n * 1e-3
     # the FP32 stage kernel also interpolates the new state to the face points
     flops_el = rhs_flops_per_element(nd) + (trace_flops_per_element(nd) if prec == "f32" else 0)
+    if args.basis == "nodal":
+        flops_el += nodal_extra_flops_per_element(nd)
     achieved = flops_el * K / rhs_avg_s / 1e12
     kname = f"rhs_kernel<{nd},double,update>" if prec == "f64" else f"stage32_kernel<{nd}>"
+    if args.basis == "nodal":
+        kname = f"nodal_rhs_kernel<{nd},update>"
     traffic, traffic_src = measured_traffic(kname, K)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_source": traffic_src, "kernel": kname,

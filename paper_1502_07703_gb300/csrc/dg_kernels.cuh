@@ -544,8 +544,8 @@ __device__ __forceinline__ void volume_passes(const T* s_tab, const T* s_u, cons
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       const int o = ((m + 1) * d::n1 + k) * d::n2 + pq;
-      xs += g[m] * s_Ua[o] + g[3 + m] * s_Ub[o];
-      zs += g[6 + m] * s_U[o];
+      xs = fma(g[m], s_Ua[o], fma(g[3 + m], s_Ub[o], xs));  // two FMAs, no separate multiply and add
+      zs = fma(g[6 + m], s_U[o], zs);
     }
     s_X[x] = xs;
     s_Zc[x] = zs;
