@@ -218,3 +218,39 @@ def test_batch_single_launch_refused_where_unavailable(torch_cuda):
     with Batch([(v, e, 2), (v, e, 2)], precision="f32") as b:  # one degree group
         with pytest.raises(PyrDGError, match="BAD_ARG"):
             b.set_launch_mode(True)
+
+
+def test_full_size_config4_sampled(torch_cuda):
+    """Config 4 as the bench runs it: 256 meshes (sizes log-uniform 48..49,152 pyramids, seed 2;
+    mesh i perturbed +-0.05h with seed 1000+i), degrees 2..6, FP32, each mesh at its own CFL
+    step, in the launch mode the setup autotuner picks. One step from the projected standing
+    wave, checked against the oracle on sampled elements of sampled meshes (one per degree,
+    the largest mesh among them) over their 6-hop neighbourhoods."""
+    from _parity import face_neighbours, patch
+    from paper_1502_07703_gb300.binding import Batch
+    from paper_1502_07703_gb300.mesh import batch_mesh_shapes
+    shapes = batch_mesh_shapes(count=256, seed=2)
+    meshes = []
+    for i, (nx, ny, nz, n) in enumerate(shapes):
+        v, e = make_pyramid_mesh(nx, ny, nz, delta=0.05, seed=1000 + i)
+        meshes.append((v, e, n))
+    with Batch(meshes, precision="f32") as b:
+        assert b.nmesh == 256 and b.ngroups == 5
+        dt = b.dt_cfl(0.5)
+        b.project(0.0)
+        b.step(1, dt)
+        picks = {}
+        for i, (_, e, n) in enumerate(meshes):
+            if n not in picks or e.shape[0] > meshes[picks[n]][1].shape[0]:
+                picks[n] = i
+        states = {i: b.get_state(i).astype(np.float64) for i in picks.values()}
+    rng = np.random.default_rng(29)
+    for n, i in sorted(picks.items()):
+        v, e, _ = meshes[i]
+        nbrs = face_neighbours(e)
+        for c in (int(rng.integers(e.shape[0])), e.shape[0] - 1):
+            p = patch(nbrs, c, 6)
+            dg = PyramidDG(v, e[p], n)
+            j = p.index(c)
+            Up = dg.lsrk4(dg.project_exact(0.0), dt[i], 1)
+            check(dg, dg.values_phi(states[i][p])[j:j + 1], dg.values_psi(Up)[j:j + 1], 1e-5, (n, i, c), elems=[j])
