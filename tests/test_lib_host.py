@@ -174,3 +174,18 @@ def test_newer_calls_check_their_arguments_on_the_host():
     assert L.pyr_dg_setup(V.ctypes.data_as(binding._c_dp), V.shape[0], E.ctypes.data_as(binding._c_i32p),
                           E.shape[0], 2, ctypes.byref(o), ctypes.byref(h)) == -1
     assert b"basis" in L.pyr_dg_last_error()
+
+
+def test_setup_refuses_sizes_beyond_its_index_range():
+    """Element counts whose face-point index K * 5(N+1)^2 or grid size would overflow 32 bits are
+    refused before the arrays are read (a one-element array stands in for the claimed size)."""
+    L = binding.lib()
+    v, e = make_pyramid_mesh(1)
+    V = np.ascontiguousarray(v, dtype=np.float64)
+    E = np.ascontiguousarray(e[:1], dtype=np.int32)
+    h = ctypes.c_void_p()
+    for K, N in ((2 ** 31 // 125 + 1, 4), (2 ** 31 // 320 + 1, 7), (2 ** 31, 1)):
+        rc = L.pyr_dg_setup(V.ctypes.data_as(binding._c_dp), V.shape[0], E.ctypes.data_as(binding._c_i32p), K, N,
+                            None, ctypes.byref(h))
+        assert rc == -1 and not h.value, (K, N, rc)
+        assert b"exceeds" in L.pyr_dg_last_error()
