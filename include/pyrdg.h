@@ -143,6 +143,21 @@ int pyr_dg_project(pyr_dg* h, double t0);
 int pyr_dg_set_state(pyr_dg* h, const void* q, int where, double t);
 int pyr_dg_get_state(pyr_dg* h, void* q, int where);
 
+/* Stage the input of the next step from host memory without waiting: q_host (K*4*Np
+ * elements of the handle's type, layout above) is copied on a copy stream of the handle
+ * into a second device buffer, so the copy overlaps work already enqueued (the current
+ * step). The next pyr_dg_step waits on the device for that copy, makes it the state, sets
+ * the time to t and zeroes the LSRK residual, then steps. Until then every other call
+ * (pyr_dg_error, pyr_dg_get_state, pyr_dg_rhs, ...) sees the current state;
+ * pyr_dg_set_state and pyr_dg_project drop a staged state, and a later stage replaces an
+ * earlier one. The paper has no counterpart (it is host-device plumbing for callers that
+ * feed a new state every step). Ownership: the caller keeps q_host. From page-locked memory
+ * the copy is asynchronous: q_host must not change until pyr_dg_sync returns, or a call
+ * that synchronises the stream (pyr_dg_error, pyr_dg_get_state) returns after the step that
+ * consumed it. Pageable memory also works, without the overlap. The first call allocates
+ * the second buffer (same size as the state); PYR_DG_ERR_NO_MEMORY if that fails. */
+int pyr_dg_stage_state(pyr_dg* h, const void* q_host, double t);
+
 /* Right-hand side dU/dt = -M^{-1}(volume + surface terms) of the state q
  * (device pointer, K*4*Np of the handle's type) into rhs (device pointer,
  * same size, must not alias q). Uses the handle's trace buffer as scratch;
@@ -237,7 +252,7 @@ int pyr_dg_time(const pyr_dg* h, double* t);
  * PYR_DG_ERR_TIMEOUT if one gave up since the last check. */
 int pyr_dg_set_tensor_mixing(pyr_dg* h, int enable);
 
-/* Wait for all work enqueued by this handle. */
+/* Wait for all work enqueued by this handle, staged state copies included. */
 int pyr_dg_sync(pyr_dg* h);
 
 /* Per-kernel timing of pyr_dg_step: with enable != 0, every stage kernel that

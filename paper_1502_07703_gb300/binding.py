@@ -62,6 +62,7 @@ _SIGNATURES = {
     "pyr_dg_project": (ctypes.c_int, [_c_h, ctypes.c_double]),
     "pyr_dg_set_state": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_int, ctypes.c_double]),
     "pyr_dg_get_state": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_int]),
+    "pyr_dg_stage_state": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_double]),
     "pyr_dg_rhs": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_void_p]),
     "pyr_dg_step": (ctypes.c_int, [_c_h, ctypes.c_int, ctypes.c_double]),
     "pyr_dg_error": (ctypes.c_int, [_c_h, _c_dp, _c_dp]),
@@ -269,6 +270,21 @@ class Solver:
     def set_state_host_ptr(self, ptr, t=0.0):
         """Set the state from a raw host pointer (e.g. a pinned torch tensor's data_ptr())."""
         _check(lib().pyr_dg_set_state(self._h, ctypes.c_void_p(ptr), PYR_DG_HOST, float(t)))
+
+    def stage_state_host_ptr(self, ptr, t=0.0):
+        """Stage the next step's input from a raw host pointer (best from page-locked memory,
+        e.g. a pinned torch tensor's data_ptr()); the copy overlaps enqueued work and the next
+        step() makes it the state. The buffer must not change until sync() (or error() /
+        get_state() after that step) returns."""
+        _check(lib().pyr_dg_stage_state(self._h, ctypes.c_void_p(ptr), float(t)))
+
+    def stage_state(self, q, t=0.0):
+        """Stage the next step's input from a numpy array (see stage_state_host_ptr). From
+        ordinary (pageable) memory the array has been copied out when the call returns, without
+        the overlap; the binding keeps a reference to it until the next stage_state()."""
+        a = np.ascontiguousarray(q, dtype=self.np_dtype).reshape(self.shape)
+        self._staged = a
+        _check(lib().pyr_dg_stage_state(self._h, a.ctypes.data, float(t)))
 
     def get_state(self, device=False):
         """Copy of the state: numpy array, or a torch CUDA tensor if device=True."""

@@ -9,6 +9,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/pyrdg.h"
@@ -157,6 +158,14 @@ cudaError_t prof_end(pyr_dg* h, size_t slot) {
 void free_all(pyr_dg* h) {
   for (cudaEvent_t ev : h->events) cudaEventDestroy(ev);
   h->events.clear();
+  if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+  if (h->q_next) cudaFree(h->q_next);
+  if (h->ev_copied) cudaEventDestroy(h->ev_copied);
+  if (h->ev_free) cudaEventDestroy(h->ev_free);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  h->q_next = nullptr;
+  h->ev_copied = h->ev_free = nullptr;
+  h->copy_stream = nullptr;
   void* ptrs[] = {h->q,    h->res,  h->tr,   h->geo,  h->gface,   h->invM,  h->tab,
                   h->tabd, h->gtab, h->ev,   h->partial, h->mapP, h->tr2,   h->dt_elem,
                   h->ecache, h->ntab, h->ntri, h->nmap};
@@ -599,6 +608,7 @@ int pyr_dg_project(pyr_dg* h, double t0) {
   CUDA_TRY(cudaMemsetAsync(h->res, 0, (size_t)h->K * h->nf * h->Np * h->tsize, h->stream));
   h->t = t0;
   h->tr_valid = false;
+  h->staged = false;  // a staged state not yet consumed is dropped
   return PYR_DG_OK;
 }
 
@@ -614,6 +624,32 @@ int pyr_dg_set_state(pyr_dg* h, const void* q, int where, double t) {
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   h->t = t;
   h->tr_valid = false;
+  h->staged = false;  // a staged state not yet consumed is dropped
+  return PYR_DG_OK;
+}
+
+int pyr_dg_stage_state(pyr_dg* h, const void* q_host, double t) {
+  if (!h || !q_host) return fail(PYR_DG_ERR_BAD_ARG, "null argument");
+  if (!std::isfinite(t)) return fail(PYR_DG_ERR_BAD_ARG, "t must be finite");
+  DeviceGuard g(h->device);
+  CUDA_TRY(g.err);
+  const size_t bytes = (size_t)h->K * h->nf * h->Np * h->tsize;
+  if (!h->copy_stream) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&h->ev_copied, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&h->ev_free, cudaEventDisableTiming));
+  }
+  if (!h->q_next && cudaMalloc(&h->q_next, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    h->q_next = nullptr;
+    return fail(PYR_DG_ERR_NO_MEMORY, "cannot allocate the staged state (%zu bytes)", bytes);
+  }
+  // the buffer's previous contents may still be read by work enqueued before the last swap
+  if (h->ev_free_recorded) CUDA_TRY(cudaStreamWaitEvent(h->copy_stream, h->ev_free, 0));
+  CUDA_TRY(cudaMemcpyAsync(h->q_next, q_host, bytes, cudaMemcpyHostToDevice, h->copy_stream));
+  CUDA_TRY(cudaEventRecord(h->ev_copied, h->copy_stream));
+  h->staged = true;
+  h->staged_t = t;
   return PYR_DG_OK;
 }
 
@@ -657,6 +693,16 @@ int pyr_dg_step(pyr_dg* h, int nsteps, double dt) {
   if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt)) return fail(PYR_DG_ERR_BAD_ARG, "need nsteps >= 0, dt > 0");
   DeviceGuard g(h->device);
   CUDA_TRY(g.err);
+  if (h->staged) {  // the staged state becomes the state once its copy has landed
+    CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_copied, 0));
+    std::swap(h->q, h->q_next);
+    CUDA_TRY(cudaEventRecord(h->ev_free, h->stream));
+    h->ev_free_recorded = true;
+    CUDA_TRY(cudaMemsetAsync(h->res, 0, (size_t)h->K * h->nf * h->Np * h->tsize, h->stream));
+    h->t = h->staged_t;
+    h->tr_valid = false;
+    h->staged = false;
+  }
   const int rc = pyrdg::enqueue_steps(h, nsteps, dt);
   if (rc != PYR_DG_OK) return rc;
   h->t += nsteps * dt;
@@ -828,6 +874,7 @@ int pyr_dg_sync(pyr_dg* h) {
   DeviceGuard g(h->device);
   CUDA_TRY(g.err);
   CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (h->copy_stream) CUDA_TRY(cudaStreamSynchronize(h->copy_stream));  // staged copies too
   if (h->use_tc) {
     const int n = h->L->tc32_timeouts();
     if (n < 0) return fail(PYR_DG_ERR_CUDA, "cannot read the tensor-core wait counter");

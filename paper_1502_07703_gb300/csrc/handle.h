@@ -59,6 +59,15 @@ struct pyr_dg {
   double* ntab = nullptr;
   int32_t* ntri = nullptr;
   int32_t* nmap = nullptr;
+  // pyr_dg_stage_state: a second state buffer that a copy stream fills while the handle's
+  // stream computes; the next pyr_dg_step waits for the copy (ev_copied), swaps it in as the
+  // state and records ev_free on the handle's stream (work enqueued before that point still
+  // reads the old buffer, which becomes q_next: the following copy waits for ev_free)
+  void* q_next = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied = nullptr, ev_free = nullptr;
+  bool staged = false, ev_free_recorded = false;
+  double staged_t = 0.0;
   // per-kernel event timing of pyr_dg_step (pyr_dg_profile)
   bool profiling = false;
   std::vector<cudaEvent_t> events;
