@@ -252,6 +252,20 @@ int pyr_dg_time(const pyr_dg* h, double* t);
  * PYR_DG_ERR_TIMEOUT if one gave up since the last check. */
 int pyr_dg_set_tensor_mixing(pyr_dg* h, int enable);
 
+/* FP32 face traces on the tensor cores (Alg. 3's interpolation of the updated state to the
+ * face points, batched over elements). The trace map Phi_f (mode n at face point g, Nfc x Np)
+ * is the same for every element and field, so the traces of 32 elements are one product
+ * T = U Phi_f^T of M = 128 rows (element x field, the state's own layout), K = Np modes,
+ * N = Nfc points: tcgen05.mma kind::tf32 with the 3-term split A_hi B_hi + A_hi B_lo +
+ * A_lo B_hi (about FP32 accuracy), FP32 accumulation in tensor memory. Phi_f is taken in
+ * FP64 from the trace kernel applied to unit states and split on the host. With enable != 0
+ * every stage runs the stage kernel without its trace passes, then this kernel writes the
+ * new state's traces into the other half of the trace pair; 0 returns to the stage kernel's
+ * own traces (the default). The first enable allocates the operator (2 NP KC NKC floats,
+ * NP = Nfc rounded up to 16). FP32 single-mesh wave handles only, else PYR_DG_ERR_BAD_ARG.
+ * Completion waits are bounded as for pyr_dg_set_tensor_mixing. */
+int pyr_dg_set_tensor_traces(pyr_dg* h, int enable);
+
 /* Wait for all work enqueued by this handle, staged state copies included. */
 int pyr_dg_sync(pyr_dg* h);
 

@@ -97,6 +97,7 @@ _SIGNATURES = {
     "pyr_dg_l2_diff": (ctypes.c_int, [_c_h, ctypes.c_void_p, ctypes.c_void_p, _c_dp, _c_dp]),
     "pyr_dg_host_nodal_points": (ctypes.c_int, [ctypes.c_int, _c_dp]),
     "pyr_dg_set_tensor_mixing": (ctypes.c_int, [_c_h, ctypes.c_int]),
+    "pyr_dg_set_tensor_traces": (ctypes.c_int, [_c_h, ctypes.c_int]),
     "pyr_dg_batch_launch_mode": (ctypes.c_int, [_c_h, _c_ip, _c_ip]),
     "pyr_dg_batch_set_launch_mode": (ctypes.c_int, [_c_h, ctypes.c_int]),
 }
@@ -329,6 +330,12 @@ class Solver:
         """FP32 wave handles at N >= 4: run the level mixing on the tensor cores (tcgen05 TF32,
         3-term split) instead of the CUDA cores."""
         _check(lib().pyr_dg_set_tensor_mixing(self._h, 1 if enable else 0))
+
+    def set_tensor_traces(self, enable=True):
+        """FP32 wave handles: interpolate each stage's new state to the face points on the tensor
+        cores (tcgen05 TF32, 3-term split, 32 elements x 4 fields per MMA tile) instead of in the
+        stage kernel."""
+        _check(lib().pyr_dg_set_tensor_traces(self._h, 1 if enable else 0))
 
     def set_error_cache(self, enable=True):
         """Store the exact fields' spatial factors for error() when they fit (the default),

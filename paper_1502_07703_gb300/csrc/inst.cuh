@@ -2,6 +2,7 @@
 #pragma once
 #include "dg_kernels.cuh"
 #include "stage32.cuh"
+#include "trace32tc.cuh"
 #include "adv32.cuh"
 #include "adv_kernels.cuh"
 #include "launch.h"
@@ -201,6 +202,18 @@ struct Impl {
     }
     return 0;
   }
+  // Face traces of an FP32 state on the tensor cores (element-batched tcgen05 product with the
+  // trace map's TF32 hi/lo parts in op, laid out as T32<N> describes).
+  static void trace32tc(int64_t K, const void* q, void* tr, const float* op, int nblocks, cudaStream_t s) {
+    if constexpr (kTC)
+      trace32tc_kernel<N><<<nblocks, T32<N>::NT, T32<N>::bytes, s>>>(K, (const float*)q, (float*)tr, op);
+  }
+  // Resident CTAs per SM of the tensor-core trace kernel: shared memory and tensor memory (the
+  // occupancy calculator does not know the latter).
+  static int blocks_per_sm_trace32tc() {
+    if constexpr (kTC) return T32<N>::CTAS;
+    return 0;
+  }
   static int tc32_timeouts() {
     int n = 0, zero = 0;
     if constexpr (kTC) {
@@ -303,10 +316,14 @@ struct Impl {
     if (e == cudaSuccess) e = smem_adv32<2>();
     if (e == cudaSuccess) e = smem_adv32<4>();
     if (e == cudaSuccess) e = smem_adv32<8>();
-    if constexpr (kTC)
+    if constexpr (kTC) {
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(stage32_kernel<N, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)S32<N, 1, true>::bytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(trace32tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)T32<N>::bytes);
+    }
     return e;
   }
   // Resident CTAs per SM of the stage kernel with epb elements per CTA; 0 if not built.
@@ -342,6 +359,12 @@ struct Impl {
     l.stage32tc = kTC ? &stage32tc : nullptr;
     l.blocks_per_sm32tc = kTC ? &blocks_per_sm32tc : nullptr;
     l.tc32_timeouts = kTC ? &tc32_timeouts : nullptr;
+    l.trace32tc = kTC ? &trace32tc : nullptr;
+    l.blocks_per_sm_trace32tc = kTC ? &blocks_per_sm_trace32tc : nullptr;
+    l.tctr_kc = T32<N>::KC;
+    l.tctr_nkc = T32<N>::NKC;
+    l.tctr_np = T32<N>::NP;
+    l.tctr_op_floats = T32<N>::op_floats;
     l.nodal_ntr = NodalDims<N>::NTR;
     l.nodal_ntab = NodalDims<N>::size;
     l.nodal_trace = sizeof(T) == 8 ? &nodal_trace : nullptr;
