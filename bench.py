@@ -292,55 +292,66 @@ def measure_form(binding, nx, delta, seed, n, precision, steps, warmup, dev):
     for _ in range(warmup):
         s.step(1, dt)
     s.sync()
-    s.profile(True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(steps):
-        s.step(1, dt)
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = ev0.elapsed_time(ev1)
-    prof = s.profile_read()
-    s.profile(False)
+
+    def timed():
+        """(ms per step, stage-kernel ms and trace-kernel ms per launch, launches) of `steps`
+        steps with the handle's current kernels, after `warmup` untimed ones."""
+        s.project(0.0)
+        for _ in range(warmup):
+            s.step(1, dt)
+        s.sync()
+        s.profile(True)
+        ev0.record(stream)
+        for _ in range(steps):
+            s.step(1, dt)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        s.sync()
+        p = s.profile_read()
+        s.profile(False)
+        return (ev0.elapsed_time(ev1) / steps, p["rhs"][0] / p["rhs"][1],
+                p["trace"][0] / p["trace"][1] if p["trace"][1] else 0.0, (p["rhs"][1] + p["trace"][1]) / steps)
+
+    ms_step, rhs_ms, tr_ms, launches = timed()
     err_abs, err_rel = s.error()
     out = {"mesh": f"{nx}^3 hexes x 6, +-{delta}h (seed {seed})", "K": s.K, "N": n, "Np": s.Np,
-           "precision": precision, "steps": steps, "ms_per_step": ms / steps,
-           "dof_updates_per_s_per_stage": s.K * s.Np * 4 * 5 * steps / (ms * 1e-3),
-           "stage_kernel_ms": prof["rhs"][0] / prof["rhs"][1],
-           "trace_kernel_ms": prof["trace"][0] / prof["trace"][1] if prof["trace"][1] else 0.0,
-           "launches_per_step": (prof["rhs"][1] + prof["trace"][1]) / steps,
+           "precision": precision, "steps": steps, "ms_per_step": ms_step,
+           "dof_updates_per_s_per_stage": s.K * s.Np * 4 * 5 / (ms_step * 1e-3),
+           "stage_kernel_ms": rhs_ms, "trace_kernel_ms": tr_ms, "launches_per_step": launches,
            "l2_rel_error_vs_exact": err_rel, "t_end": (warmup + steps) * dt}
-    if precision == "f32":  # the stage kernel against the FP32 FMA and HBM peaks
-        t_s = out["stage_kernel_ms"] * 1e-3
+    if precision == "f32":  # the stage (stage kernel, and the trace kernel where it runs) against the peaks
+        tensor_traces = tr_ms > 0.0
+        out["tensor_traces"] = tensor_traces
+        t_s = (rhs_ms + tr_ms) * 1e-3  # one RK stage
         flops = (rhs_flops_per_element(n) + trace_flops_per_element(n)) * s.K / t_s / 1e12
         gbs = stage_bytes_per_element(n, 4) * s.K / t_s / 1e9
         peak = binding.fma_peak("f32")
-        out["stage_kernel_roofline"] = {"achieved_tflops": flops, "fp32_fma_peak_tflops": peak,
+        out["stage_kernel_roofline"] = {"stage_ms": t_s * 1e3, "achieved_tflops": flops, "fp32_fma_peak_tflops": peak,
                                         "alu_frac": flops / peak, "algorithmic_bytes_per_element":
                                         stage_bytes_per_element(n, 4), "achieved_gbs": gbs,
                                         "hbm_peak_gbs": HBM_GBS, "hbm_peak_kind": HBM_KIND,
                                         "hbm_frac": gbs / HBM_GBS}
+        if tensor_traces:  # the trace kernel alone: state read, traces written
+            tb = 4 * s.Np * 4 + s.Nfc * 16
+            out["trace_kernel_roofline"] = {
+                "kernel": f"trace32tc_kernel<{n}>", "bytes_per_element": tb,
+                "achieved_gbs": tb * s.K / (tr_ms * 1e-3) / 1e9, "hbm_frac": tb * s.K / (tr_ms * 1e-3) / 1e9 / HBM_GBS}
+        # the other trace path: the stage kernel's own trace passes, or the tensor-core kernel
+        s.set_tensor_traces(not tensor_traces)
+        o_step, o_rhs, o_tr, _ = timed()
+        s.set_tensor_traces(tensor_traces)
+        out["other_trace_path"] = {"tensor_traces": not tensor_traces, "ms_per_step": o_step,
+                                   "stage_ms": o_rhs + o_tr,
+                                   "dof_updates_per_s_per_stage": s.K * s.Np * 4 * 5 / (o_step * 1e-3)}
         if n >= 4:  # the same stage with the level mixing on the tensor cores (tcgen05, TF32 x 3)
             s.set_tensor_mixing(True)
-            s.project(0.0)
-            for _ in range(warmup):
-                s.step(1, dt)
-            s.sync()
-            s.profile(True)
-            ev0.record(stream)
-            for _ in range(steps):
-                s.step(1, dt)
-            ev1.record(stream)
-            torch.cuda.synchronize(dev)
-            s.sync()
-            ms_tc = ev0.elapsed_time(ev1)
-            prof_tc = s.profile_read()
-            s.profile(False)
-            t_tc = prof_tc["rhs"][0] / prof_tc["rhs"][1] * 1e-3
+            ms_tc, rhs_tc, tr_tc, _ = timed()
+            t_tc = (rhs_tc + tr_tc) * 1e-3
             out["tensor_mixing"] = {
-                "ms_per_step": ms_tc / steps, "stage_kernel_ms": t_tc * 1e3,
-                "dof_updates_per_s_per_stage": s.K * s.Np * 4 * 5 * steps / (ms_tc * 1e-3),
+                "ms_per_step": ms_tc, "stage_kernel_ms": rhs_tc, "trace_kernel_ms": tr_tc,
+                "dof_updates_per_s_per_stage": s.K * s.Np * 4 * 5 / (ms_tc * 1e-3),
                 "hbm_frac": stage_bytes_per_element(n, 4) * s.K / t_tc / 1e9 / HBM_GBS,
                 "note": "level mixing as tcgen05.mma kind::tf32 (A_hi B_hi + A_hi B_lo + A_lo B_hi), FP32 accumulation "
                         "in tensor memory, one M = 128 chain per element"}
@@ -679,8 +690,10 @@ def main():
     tr_ms, tr_n = prof["trace"]
     peak = binding.fma_peak(prec)
     rhs_avg_s = rhs_ms / rhs_n * 1e-3
-    # the FP32 stage kernel also interpolates the new state to the face points
-    flops_el = rhs_flops_per_element(nd) + (trace_flops_per_element(nd) if prec == "f32" else 0)
+    # the FP32 stage kernel also interpolates the new state to the face points, unless that runs
+    # as the tensor-core trace kernel (one launch per stage beside it: trace flops left out)
+    f32_own_traces = prec == "f32" and tr_n <= 1
+    flops_el = rhs_flops_per_element(nd) + (trace_flops_per_element(nd) if f32_own_traces else 0)
     if args.basis == "nodal":
         flops_el += nodal_extra_flops_per_element(nd)
     achieved = flops_el * K / rhs_avg_s / 1e12

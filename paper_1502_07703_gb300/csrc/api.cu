@@ -286,6 +286,83 @@ int enqueue_steps(pyr_dg* h, int nsteps, double dt) {
 }
 }  // namespace pyrdg
 
+namespace {
+// Round a float to TF32 (10 explicit mantissa bits), to nearest with ties away from zero.
+float tf32_round(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  b = (b + 0x1000u) & 0xFFFFE000u;
+  float y;
+  std::memcpy(&y, &b, 4);
+  return y;
+}
+
+// Operand of the tensor-core trace kernel: the dense trace map Phi_f (mode n at face point g)
+// in FP64, obtained by applying the FP64 trace kernel to the Np unit states (pseudo-element n
+// holds mode n in every field), split into TF32 hi and lo parts and laid out in NKC pieces of
+// KC mode columns, each NP x KC (rows = face points) in the K-major no-swizzle operand layout.
+int build_trace_operator(pyr_dg* h) {
+  const pyrdg::Launchers* L64 = pyrdg::get_launchers(h->N, 0);
+  if (!L64) return fail(PYR_DG_ERR_UNSUPPORTED_N, "no FP64 launchers for N = %d", h->N);
+  CUDA_TRY(L64->prepare());
+  const int Np = h->Np, Nfc = h->Nfc;
+  const size_t nq = (size_t)Np * 4 * Np, ntr = (size_t)Np * Nfc * 4;
+  std::vector<double> unit(nq, 0.0), tr(ntr);
+  for (int n = 0; n < Np; ++n)
+    for (int f = 0; f < 4; ++f) unit[((size_t)n * 4 + f) * Np + n] = 1.0;
+  double *dq = nullptr, *dtr = nullptr;
+  CUDA_TRY(cudaMalloc(&dq, nq * 8));
+  if (cudaMalloc(&dtr, ntr * 8) != cudaSuccess) {
+    cudaFree(dq);
+    return fail(PYR_DG_ERR_NO_MEMORY, "tensor-core traces: scratch allocation failed");
+  }
+  cudaError_t e = cudaMemcpyAsync(dq, unit.data(), nq * 8, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) {
+    L64->trace(Np, dq, h->tabd, dtr, h->stream);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tr.data(), dtr, ntr * 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(dq);
+  cudaFree(dtr);
+  if (e != cudaSuccess) return fail(PYR_DG_ERR_CUDA, "tensor-core traces: trace map: %s", cudaGetErrorString(e));
+  const int KC = h->L->tctr_kc, NKC = h->L->tctr_nkc, NP = h->L->tctr_np;
+  std::vector<float> op(h->L->tctr_op_floats, 0.f);
+  for (int kc = 0; kc < NKC; ++kc) {
+    float* hi = op.data() + (size_t)kc * 2 * NP * KC;
+    float* lo = hi + (size_t)NP * KC;
+    for (int g = 0; g < Nfc; ++g)
+      for (int k = 0; k < KC; ++k) {
+        const int n = kc * KC + k;
+        if (n >= Np) continue;
+        const double v = tr[((size_t)n * Nfc + g) * 4];  // field 0 of pseudo-element n
+        const float vh = tf32_round((float)v);
+        const size_t o = (size_t)(g >> 3) * (8 * KC) + (k >> 2) * 32 + (g & 7) * 4 + (k & 3);
+        hi[o] = vh;
+        lo[o] = tf32_round((float)(v - (double)vh));
+      }
+  }
+  CUDA_TRY(cudaMalloc(&h->tctr_op, op.size() * sizeof(float)));
+  CUDA_TRY(cudaMemcpy(h->tctr_op, op.data(), op.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return PYR_DG_OK;
+}
+}  // namespace
+
+namespace {
+int enable_tensor_traces(pyr_dg* h) {
+  if (!h->tctr_op) {
+    const int rc = build_trace_operator(h);
+    if (rc != PYR_DG_OK) return rc;
+  }
+  int nsm = 1;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  const int64_t tiles = (h->K + 31) / 32;
+  h->tctr_blocks = (int)std::min<int64_t>(tiles, (int64_t)nsm * h->L->blocks_per_sm_trace32tc());
+  h->use_tctr = true;
+  return PYR_DG_OK;
+}
+}  // namespace
+
 extern "C" {
 
 void pyr_dg_default_opts(pyr_dg_opts* o) {
@@ -578,6 +655,18 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   if (h->equation == PYR_DG_WAVE) {
     void* p = nullptr;
     if (noalloc_scratch_address(h->device, &p) != cudaSuccess) cudaGetLastError();
+  }
+  // FP32 wave handles: the new state's face traces on the tensor cores where that is faster,
+  // at the degrees the launchers mark and on meshes of at least 40,000 pyramids (measured: from
+  // about 8 tiles of 32 elements per SM up the second launch per stage pays for itself)
+  if (h->use_stage32 && h->equation == PYR_DG_WAVE && h->basis == PYR_DG_MODAL && h->L->tctr_default &&
+      h->K >= 40000) {
+    const int rc = enable_tensor_traces(h);
+    if (rc != PYR_DG_OK) {
+      free_all(h);
+      delete h;
+      return rc;
+    }
   }
   *out = h;
   return PYR_DG_OK;
@@ -920,67 +1009,6 @@ int pyr_dg_set_tensor_mixing(pyr_dg* h, int enable) {
   return PYR_DG_OK;
 }
 
-namespace {
-// Round a float to TF32 (10 explicit mantissa bits), to nearest with ties away from zero.
-float tf32_round(float x) {
-  uint32_t b;
-  std::memcpy(&b, &x, 4);
-  b = (b + 0x1000u) & 0xFFFFE000u;
-  float y;
-  std::memcpy(&y, &b, 4);
-  return y;
-}
-
-// Operand of the tensor-core trace kernel: the dense trace map Phi_f (mode n at face point g)
-// in FP64, obtained by applying the FP64 trace kernel to the Np unit states (pseudo-element n
-// holds mode n in every field), split into TF32 hi and lo parts and laid out in NKC pieces of
-// KC mode columns, each NP x KC (rows = face points) in the K-major no-swizzle operand layout.
-int build_trace_operator(pyr_dg* h) {
-  const pyrdg::Launchers* L64 = pyrdg::get_launchers(h->N, 0);
-  if (!L64) return fail(PYR_DG_ERR_UNSUPPORTED_N, "no FP64 launchers for N = %d", h->N);
-  CUDA_TRY(L64->prepare());
-  const int Np = h->Np, Nfc = h->Nfc;
-  const size_t nq = (size_t)Np * 4 * Np, ntr = (size_t)Np * Nfc * 4;
-  std::vector<double> unit(nq, 0.0), tr(ntr);
-  for (int n = 0; n < Np; ++n)
-    for (int f = 0; f < 4; ++f) unit[((size_t)n * 4 + f) * Np + n] = 1.0;
-  double *dq = nullptr, *dtr = nullptr;
-  CUDA_TRY(cudaMalloc(&dq, nq * 8));
-  if (cudaMalloc(&dtr, ntr * 8) != cudaSuccess) {
-    cudaFree(dq);
-    return fail(PYR_DG_ERR_NO_MEMORY, "tensor-core traces: scratch allocation failed");
-  }
-  cudaError_t e = cudaMemcpyAsync(dq, unit.data(), nq * 8, cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) {
-    L64->trace(Np, dq, h->tabd, dtr, h->stream);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(tr.data(), dtr, ntr * 8, cudaMemcpyDeviceToHost, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  cudaFree(dq);
-  cudaFree(dtr);
-  if (e != cudaSuccess) return fail(PYR_DG_ERR_CUDA, "tensor-core traces: trace map: %s", cudaGetErrorString(e));
-  const int KC = h->L->tctr_kc, NKC = h->L->tctr_nkc, NP = h->L->tctr_np;
-  std::vector<float> op(h->L->tctr_op_floats, 0.f);
-  for (int kc = 0; kc < NKC; ++kc) {
-    float* hi = op.data() + (size_t)kc * 2 * NP * KC;
-    float* lo = hi + (size_t)NP * KC;
-    for (int g = 0; g < Nfc; ++g)
-      for (int k = 0; k < KC; ++k) {
-        const int n = kc * KC + k;
-        if (n >= Np) continue;
-        const double v = tr[((size_t)n * Nfc + g) * 4];  // field 0 of pseudo-element n
-        const float vh = tf32_round((float)v);
-        const size_t o = (size_t)(g >> 3) * (8 * KC) + (k >> 2) * 32 + (g & 7) * 4 + (k & 3);
-        hi[o] = vh;
-        lo[o] = tf32_round((float)(v - (double)vh));
-      }
-  }
-  CUDA_TRY(cudaMalloc(&h->tctr_op, op.size() * sizeof(float)));
-  CUDA_TRY(cudaMemcpy(h->tctr_op, op.data(), op.size() * sizeof(float), cudaMemcpyHostToDevice));
-  return PYR_DG_OK;
-}
-}  // namespace
 
 int pyr_dg_set_tensor_traces(pyr_dg* h, int enable) {
   if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
@@ -988,21 +1016,11 @@ int pyr_dg_set_tensor_traces(pyr_dg* h, int enable) {
     h->use_tctr = false;
     return PYR_DG_OK;
   }
-  if (!h->use_stage32 || h->equation != PYR_DG_WAVE || !h->L->trace32tc)
+  if (!h->use_stage32 || h->equation != PYR_DG_WAVE || h->basis != PYR_DG_MODAL || !h->L->trace32tc)
     return fail(PYR_DG_ERR_BAD_ARG, "tensor-core traces need an FP32 wave handle");
-  if (h->dt_elem) return fail(PYR_DG_ERR_BAD_ARG, "tensor-core traces are for single meshes");
   DeviceGuard g(h->device);
   CUDA_TRY(g.err);
-  if (!h->tctr_op) {
-    const int rc = build_trace_operator(h);
-    if (rc != PYR_DG_OK) return rc;
-  }
-  int nsm = 1;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
-  const int64_t tiles = (h->K + 31) / 32;
-  h->tctr_blocks = (int)std::min<int64_t>(tiles, (int64_t)nsm * h->L->blocks_per_sm_trace32tc());
-  h->use_tctr = true;
-  return PYR_DG_OK;
+  return enable_tensor_traces(h);
 }
 
 int pyr_dg_profile(pyr_dg* h, int enable) {

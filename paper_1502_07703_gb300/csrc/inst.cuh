@@ -206,12 +206,18 @@ struct Impl {
   // trace map's TF32 hi/lo parts in op, laid out as T32<N> describes).
   static void trace32tc(int64_t K, const void* q, void* tr, const float* op, int nblocks, cudaStream_t s) {
     if constexpr (kTC)
-      trace32tc_kernel<N><<<nblocks, T32<N>::NT, T32<N>::bytes, s>>>(K, (const float*)q, (float*)tr, op);
+      trace32tc_kernel<N><<<nblocks, T32<N>::NT, T32<N>::launch_bytes, s>>>(K, (const float*)q, (float*)tr, op);
   }
   // Resident CTAs per SM of the tensor-core trace kernel: shared memory and tensor memory (the
   // occupancy calculator does not know the latter).
   static int blocks_per_sm_trace32tc() {
-    if constexpr (kTC) return T32<N>::CTAS;
+    if constexpr (kTC) {
+      cudaFuncAttributes a;
+      int n = T32<N>::CTAS;
+      if (cudaFuncGetAttributes(&a, trace32tc_kernel<N>) == cudaSuccess && a.numRegs > 0)
+        n = std::min(n, 65536 / (((a.numRegs + 7) / 8 * 8) * T32<N>::NT));
+      return n > 0 ? n : 1;
+    }
     return 0;
   }
   static int tc32_timeouts() {
@@ -322,7 +328,7 @@ struct Impl {
                                  (int)S32<N, 1, true>::bytes);
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(trace32tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)T32<N>::bytes);
+                                 (int)T32<N>::launch_bytes);
     }
     return e;
   }
@@ -361,10 +367,13 @@ struct Impl {
     l.tc32_timeouts = kTC ? &tc32_timeouts : nullptr;
     l.trace32tc = kTC ? &trace32tc : nullptr;
     l.blocks_per_sm_trace32tc = kTC ? &blocks_per_sm_trace32tc : nullptr;
-    l.tctr_kc = T32<N>::KC;
-    l.tctr_nkc = T32<N>::NKC;
+    l.tctr_kc = T32<N>::BK;
+    l.tctr_nkc = T32<N>::NBP;
     l.tctr_np = T32<N>::NP;
     l.tctr_op_floats = T32<N>::op_floats;
+    // measured (stage without its trace passes + this kernel, against the stage kernel's own
+    // traces) on 48,000 to 196,608 pyramids: faster at N = 2 to 6, slower at N = 1, level at N = 7
+    l.tctr_default = kTC && N >= 2 && N <= 6;
     l.nodal_ntr = NodalDims<N>::NTR;
     l.nodal_ntab = NodalDims<N>::size;
     l.nodal_trace = sizeof(T) == 8 ? &nodal_trace : nullptr;

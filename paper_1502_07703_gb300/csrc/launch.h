@@ -81,12 +81,13 @@ struct Launchers {
   // Read and clear the count of its completion waits that gave up (0 in normal operation).
   int (*tc32_timeouts)();
   // FP32 face traces on the tensor cores (element-batched: T = U Phi_f^T over tiles of 32
-  // elements x 4 fields); null for double. op: the trace map's TF32 hi and lo parts, NKC pieces
-  // of K = tctr_kc mode columns, each hi then lo, NP x KC in the K-major no-swizzle operand
-  // layout (core matrices of 8 rows x 4 columns), op_floats floats in all.
+  // elements x 4 fields); null for double. op: the trace map's TF32 hi and lo parts, tctr_nkc
+  // pieces of tctr_kc mode columns, each hi then lo, NP x tctr_kc in the K-major no-swizzle
+  // operand layout (core matrices of 8 rows x 4 columns), op_floats floats in all.
   void (*trace32tc)(int64_t K, const void* q, void* tr, const float* op, int nblocks, cudaStream_t s);
   int (*blocks_per_sm_trace32tc)();
   int tctr_kc, tctr_nkc, tctr_np;
+  int tctr_default;  // FP32 wave handles start with these traces (measured faster at this degree)
   size_t tctr_op_floats;
   int nodal_ntr;      // trace points per element of the nodal variant
   int nodal_ntab;     // doubles in its table

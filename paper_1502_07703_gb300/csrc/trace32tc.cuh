@@ -7,196 +7,288 @@
 //  - tcgen05.mma kind::tf32 with the 3-term split A_hi B_hi + A_hi B_lo + A_lo B_hi (about FP32
 //    accuracy) and FP32 accumulation in TMEM: 128 lanes (the tile's rows) x the padded N columns;
 //  - Phi_f's hi and lo parts are built on the host from the FP64 trace map and stored in the
-//    operand layout (K-major, no swizzle), cut along K into NKC pieces that fit shared memory;
-//    with one piece it stays resident for the CTA's lifetime, else each piece is brought in per
-//    tile (from L2);
-//  - persistent CTAs of 128 threads; a tile's state arrives by cp.async (the next tile's while
-//    the current one is multiplied, where two buffers fit), then each thread converts its own row
-//    into the TF32 hi and lo operand tiles;
-//  - thread t reads TMEM lane t (its row: element t / 4, field t % 4) and stores that field of its
-//    element's face points into the trace layout (K x Nfc x 4), four threads filling each 16-byte
-//    point.
-// The completion waits are bounded like the tensor-core stage kernel's; a wait that gives up is
-// counted in g_tc32_timeouts and leaves the rest of the CTA's tiles unwritten.
+//    operand layout (K-major, no swizzle). At N <= 5 the whole map stays in shared memory for
+//    the CTA's lifetime; above that it is cut along K into pieces of 32 modes brought in per tile
+//    (from L2) into two alternating slots. The state side is cut the same way at N >= 5;
+//  - warp-specialised persistent CTAs of 256 threads: warps 4-7 produce (thread r converts row r
+//    of each operand piece from the state into TF32 hi and lo parts, the operator piece arrives
+//    by cp.async, and thread 0 of the group issues the MMAs), warps 0-3 drain the accumulators
+//    (thread t reads TMEM lane t, its row, and stores that field of its element's face points
+//    into the trace layout K x Nfc x 4). Two operand slots and, where TMEM holds them, two
+//    accumulators let the conversion of the next piece and the stores of the previous tile
+//    overlap the MMAs; mbarriers hand slots and accumulators between the roles.
+// Every wait is bounded like the tensor-core stage kernel's; a wait that gives up is counted in
+// g_tc32_timeouts, and the CTA stops (its remaining tiles are left unwritten).
 #pragma once
 
 #include "stage32.cuh"
 
 namespace pyrdg {
 
+__device__ __forceinline__ void tc_mbar_arrive(uint32_t mbar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
+}
+
+// Barrier of the 128 producer threads (named barrier 1) that also ORs a flag across them, so
+// that every producer takes the same branch after it.
+__device__ __forceinline__ bool producers_sync_or(bool v) {
+  uint32_t out;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(out)
+      : "r"((uint32_t)v)
+      : "memory");
+  return out != 0;
+}
+
+// 4 x 4 transpose within each quad of lanes: lane u of the quad holds a[j] = M[j][u] on entry
+// and M[u][j] on exit (two butterfly exchanges of two values each).
+__device__ __forceinline__ void quad_transpose(float (&a)[4], int u) {
+#pragma unroll
+  for (int sb = 1; sb <= 2; sb <<= 1) {
+    const bool hi = (u & sb) != 0;
+    // the two entries whose index bit sb differs from this lane's go to the partner lane u ^ sb
+    const float s0 = hi ? a[0] : a[sb];
+    const float s1 = hi ? a[sb == 1 ? 2 : 1] : a[3];
+    const float r0 = __shfl_xor_sync(0xffffffffu, s0, sb);
+    const float r1 = __shfl_xor_sync(0xffffffffu, s1, sb);
+    if (sb == 1) {
+      if (hi) {
+        a[0] = r0;
+        a[2] = r1;
+      } else {
+        a[1] = r0;
+        a[3] = r1;
+      }
+    } else {
+      if (hi) {
+        a[0] = r0;
+        a[1] = r1;
+      } else {
+        a[2] = r0;
+        a[3] = r1;
+      }
+    }
+  }
+}
+
 template <int N>
 struct T32 {
   using d = Dims<N>;
-  static constexpr int NT = 128;
+  static constexpr int NT = 256;                        // warps 0-3 drain, 4-7 produce
   static constexpr int EPT = 32;                        // elements per tile (x 4 fields = M)
   static constexpr int KP = (d::Np + 7) / 8 * 8;        // modes, padded to the TF32 K step
   static constexpr int NP = (d::Nfc + 15) / 16 * 16;    // face points, padded (MMA N step)
-  static constexpr int KC = N <= 4 ? KP : N <= 6 ? 48 : 32;  // K columns per operand piece
-  static constexpr int NKC = (KP + KC - 1) / KC;        // pieces
+  static constexpr bool BRES = N <= 5;                  // operator resident for the CTA's lifetime
+  static constexpr int KC = N <= 4 ? KP : 32;           // mode columns per A piece
+  static constexpr int NKC = (KP + KC - 1) / KC;        // A pieces per tile
+  static constexpr int BK = BRES ? NKC * KC : KC;       // mode columns of the operator in shared memory
+  static constexpr int NBP = BRES ? 1 : NKC;            // operator pieces (of BK columns)
   static constexpr int NCH = (NP + 255) / 256;          // MMA column chunks (N <= 256 each)
   static constexpr int CN = (NP / NCH + 15) / 16 * 16;  // columns per chunk
   static_assert(CN * NCH == NP, "column chunks must tile the padded face points");
-  static constexpr int TCOLS = NP <= 32 ? 32 : NP <= 64 ? 64 : NP <= 128 ? 128 : NP <= 256 ? 256 : 512;
-  static constexpr int RB = N <= 5 ? 2 : 1;             // state buffers (2: next tile prefetched)
-  // shared-memory layout (floats)
-  static constexpr size_t rawsz = (size_t)EPT * 4 * d::Np;
-  static constexpr size_t raw = 0;
-  static constexpr size_t ahi = (raw + RB * rawsz + 31) / 32 * 32;
-  static constexpr size_t alo = ahi + 128 * KC;
-  static constexpr size_t bhi = alo + 128 * KC;
-  static constexpr size_t blo = bhi + (size_t)NP * KC;
-  static constexpr size_t bar = blo + (size_t)NP * KC;  // mbarrier (2 words), TMEM address, flag
-  static constexpr size_t bytes = (bar + 4) * sizeof(float);
+  static constexpr int NACC = 2 * NP <= 512 ? 2 : 1;    // accumulators in TMEM
+  static constexpr int TCOLS = NACC * NP <= 32 ? 32 : NACC * NP <= 64 ? 64 : NACC * NP <= 128 ? 128
+                             : NACC * NP <= 256 ? 256 : 512;
+  // shared-memory layout (floats): two A slots (hi, lo), the operator slots (hi, lo), mbarriers
+  static constexpr size_t asz = (size_t)128 * KC, bsz = (size_t)NP * BK;
+  static constexpr int NBS = BRES ? 1 : 2;
+  static constexpr size_t a0 = 0;
+  static constexpr size_t b0 = a0 + 2 * 2 * asz;
+  static constexpr size_t bars = b0 + NBS * 2 * bsz;    // 6 mbarriers, TMEM address, stop flag
+  static constexpr size_t bytes = (bars + 16) * sizeof(float);
   static_assert(bytes <= 227 * 1024, "tensor-core trace kernel shared memory");
-  // resident CTAs per SM (shared memory, at most 16 of 128 threads); their TMEM must fit the
-  // SM's 512 columns, or an allocation would wait for another CTA to finish
-  static constexpr int CTAS = (int)((228 * 1024) / (bytes + 1024)) < 16 ? (int)((228 * 1024) / (bytes + 1024)) : 16;
-  static_assert(CTAS >= 1 && TCOLS * CTAS <= 512, "tensor memory per SM");
-  // the operator buffer: per piece, hi then lo, each NP x KC in the operand layout
-  static constexpr size_t op_floats = (size_t)NKC * 2 * NP * KC;
+  // resident CTAs per SM: at most 8 of 256 threads, and as many as their TMEM columns fit in
+  // the SM's 512 (an allocation beyond that would wait for another CTA to exit); the launch
+  // asks for enough shared memory that no more than that many fit
+  static constexpr int CTAS_TMEM = 512 / TCOLS < 8 ? 512 / TCOLS : 8;
+  static constexpr size_t pad_bytes = (228 * 1024) / (CTAS_TMEM + 1) - 1024 + 1024;
+  static constexpr size_t launch_bytes = bytes > pad_bytes ? bytes : pad_bytes;
+  static constexpr int CTAS_SMEM = (int)((228 * 1024) / (launch_bytes + 1024));
+  static constexpr int CTAS = CTAS_SMEM < CTAS_TMEM ? CTAS_SMEM : CTAS_TMEM;
+  static_assert(CTAS >= 1 && CTAS * TCOLS <= 512, "tensor memory per SM");
+  static_assert(launch_bytes <= 227 * 1024, "padded shared memory");
+  // the operator buffer: per piece, hi then lo, each NP x BK in the operand layout
+  static constexpr size_t op_floats = (size_t)NBP * 2 * NP * BK;
 };
 
 template <int N>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 1)
     trace32tc_kernel(int64_t K, const float* __restrict__ q, float* __restrict__ tr, const float* __restrict__ op) {
   using T = T32<N>;
   using d = Dims<N>;
-  constexpr int Np = d::Np, Nfc = d::Nfc, KC = T::KC, NKC = T::NKC, NP = T::NP, EPT = T::EPT;
+  constexpr int Np = d::Np, Nfc = d::Nfc, KC = T::KC, NKC = T::NKC, NP = T::NP, EPT = T::EPT, NACC = T::NACC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sm = reinterpret_cast<float*>(smem_raw);
-  float* Ahi = sm + T::ahi;
-  float* Alo = sm + T::alo;
-  float* Bhi = sm + T::bhi;
-  uint32_t* bar = reinterpret_cast<uint32_t*>(sm + T::bar);
-  const uint32_t mbar = smem_addr(bar);
-  uint32_t* flag = bar + 3;
+  uint64_t* mb = reinterpret_cast<uint64_t*>(sm + T::bars);  // slot_free[2], acc_full[2], acc_empty[2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mb + 6);
+  volatile uint32_t* stop = tslot + 1;
+  const uint32_t slot_free0 = smem_addr(mb), acc_full0 = smem_addr(mb + 2), acc_empty0 = smem_addr(mb + 4);
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
-    tc_mbar_init(mbar, 1);
-    *flag = 0u;
+    for (int i = 0; i < 2; ++i) {
+      tc_mbar_init(slot_free0 + 8 * i, 1);
+      tc_mbar_init(acc_full0 + 8 * i, 1);
+      tc_mbar_init(acc_empty0 + 8 * i, 128);
+    }
+    *stop = 0u;
   }
-  if (tid < 32) tc_alloc(bar + 2, T::TCOLS);
+  if (warp == 0) tc_alloc(tslot, T::TCOLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = bar[2];
+  const uint32_t tmem = *tslot;
   const int64_t ntiles = (K + EPT - 1) / EPT;
-
-  // operator piece kc into Bhi/Blo (contiguous hi then lo, 16-byte copies)
-  auto load_op = [&](int kc) {
-    const float* src = op + (size_t)kc * 2 * NP * KC;
-    for (int x = tid; x < 2 * NP * KC / 4; x += T::NT) cp_async16(Bhi + 4 * x, src + 4 * x);
-  };
-  // state of the tile starting at element e0 (its elements in the mesh) into buffer b
-  auto load_tile = [&](int64_t e0, int b) {
-    const int ne = (int)min((int64_t)EPT, K - e0);
-    float* dst = sm + T::raw + b * T::rawsz;
-    const float* src = q + e0 * 4 * Np;
-    for (int x = tid; x < ne * Np; x += T::NT) cp_async16(dst + 4 * x, src + 4 * x);  // 4 Np floats per element
-  };
-  if constexpr (NKC == 1) load_op(0);
-  if (blockIdx.x < ntiles) load_tile((int64_t)blockIdx.x * EPT, 0);
-  cp_async_commit();
-
   bool ok = true;
-  uint32_t phase = 0;  // completions waited for so far
-  int it = 0;
-  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
-    const int64_t e0 = tile * EPT;
-    const int ne = (int)min((int64_t)EPT, K - e0);
-    const float* rawc = sm + T::raw + (T::RB == 2 ? (it & 1) : 0) * T::rawsz;
-    const int64_t tnext = tile + gridDim.x;
-    for (int kc = 0; kc < NKC && ok; ++kc) {
-      if constexpr (NKC > 1) {
-        load_op(kc);
-        cp_async_commit();
-      }
-      cp_async_wait_all();  // this thread's copies of the tile (and the piece) have landed
-      __syncthreads();      // ... everyone's; the previous MMAs and TMEM reads are complete
-      if (kc == 0 && T::RB == 2 && tnext < ntiles) {  // the next tile into the other buffer
-        load_tile(tnext * EPT, (it + 1) & 1);
-        cp_async_commit();
-      }
-      // row tid of the operand tiles: field tid % 4 of element tid / 4, modes [kc KC, kc KC + KC)
-      {
-        const int r = tid;
-        const bool live = (r >> 2) < ne;
-        const float* src = rawc + r * Np;
-#pragma unroll 4
-        for (int c4 = 0; c4 < KC / 4; ++c4) {
-          float h[4], l[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int n = kc * KC + 4 * c4 + i;
-            const float x = (live && n < Np) ? src[n] : 0.f;
-            tf32_split(x, h[i], l[i]);
-          }
-          const int o = tc_offset<KC>(r, 4 * c4);
-          *reinterpret_cast<float4*>(Ahi + o) = make_float4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<float4*>(Alo + o) = make_float4(l[0], l[1], l[2], l[3]);
-        }
-      }
-      tc_fence_smem();
-      __syncthreads();
-      if (T::RB == 1 && kc == NKC - 1 && tnext < ntiles) {  // the state buffer is free: next tile
-        load_tile(tnext * EPT, 0);
-        cp_async_commit();
-      }
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t a_hi = smem_addr(Ahi), a_lo = smem_addr(Alo), b_hi = smem_addr(Bhi),
-                       b_lo = b_hi + NP * KC * 4;
-        constexpr uint32_t idesc = tc_idesc_tf32(128, T::CN);
-#pragma unroll
-        for (int ch = 0; ch < T::NCH; ++ch) {
-          const uint32_t boff = (uint32_t)ch * T::CN * KC * 4;  // CN rows of B
-#pragma unroll
-          for (int st = 0; st < KC / 8; ++st) {
-            const uint64_t ah = tc_smem_desc(a_hi + 256 * st, 128, 32 * KC);
-            const uint64_t al = tc_smem_desc(a_lo + 256 * st, 128, 32 * KC);
-            const uint64_t bh = tc_smem_desc(b_hi + boff + 256 * st, 128, 32 * KC);
-            const uint64_t bl = tc_smem_desc(b_lo + boff + 256 * st, 128, 32 * KC);
-            const uint32_t dcol = tmem + ch * T::CN;
-            tc_mma_tf32(dcol, ah, bh, idesc, kc > 0 || st > 0);
-            tc_mma_tf32(dcol, ah, bl, idesc, true);
-            tc_mma_tf32(dcol, al, bh, idesc, true);
-          }
-        }
-        tc_commit(mbar);
-        if (!tc_mbar_wait(mbar, phase & 1, kTcWaitPolls)) *flag = 1u;
-      }
-      ++phase;
-      __syncthreads();
-      ok = *flag == 0u;
-      tc_fence_after();
+
+  if (warp >= 4) {
+    // ---- producers: operand pieces and the MMAs
+    const int r = tid - 128;  // operand row: field r % 4 of element r / 4 of the tile
+    float* Bs = sm + T::b0;
+    if constexpr (T::BRES) {  // the operator, once
+      for (int x = r; x < (int)(2 * T::bsz / 4); x += 128) cp_async16(Bs + 4 * x, op + 4 * x);
+      cp_async_commit();
+      cp_async_wait_all();
     }
-    if (!ok) break;
-    // thread tid: TMEM lane tid = field f of element el; its face points to the trace layout
+    int pc = 0, i = 0;
+    uint32_t last_free = 0;  // the last commit's slot barrier and parity (teardown after a stop)
+    int last_use = -1;
+    for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++i) {
+      const int64_t e0 = tile * EPT;
+      const int ne = (int)min((int64_t)EPT, K - e0);
+      const int acc = i % NACC;
+      const int64_t tn = tile + gridDim.x;
+      if (tn < ntiles)  // the next tile's state into L2
+        prefetch_l2(q + tn * EPT * 4 * Np, sizeof(float) * 4 * Np * (size_t)min((int64_t)EPT, K - tn * EPT), r, 128);
+      for (int kc = 0; kc < NKC && ok; ++kc, ++pc) {
+        const int slot = pc & 1, use = pc >> 1;
+        // the slot's previous piece has been multiplied
+        if (use >= 1 && !tc_mbar_wait(slot_free0 + 8 * slot, (use - 1) & 1, kTcWaitPolls)) *stop = 1u;
+        float* Ah = sm + T::a0 + slot * 2 * T::asz;
+        float* Al = Ah + T::asz;
+        if constexpr (!T::BRES) {
+          float* Bh = Bs + slot * 2 * T::bsz;
+          const float* ps = op + (size_t)kc * 2 * T::bsz;
+          for (int x = r; x < (int)(2 * T::bsz / 4); x += 128) cp_async16(Bh + 4 * x, ps + 4 * x);
+          cp_async_commit();
+        }
+        // operand rows of this piece: lane l of producer warp w takes rows 32 w + 8 o + (l % 8)
+        // and column groups 4 cb + l / 8 (4 modes each), so that each 8-lane store fills one
+        // core matrix; every load of the piece is issued before any conversion
+        {
+          const int lane = r & 31, wq = r >> 5, ro = lane & 7, cq = lane >> 3;
+          constexpr int NCB = (KC / 4 + 3) / 4;  // column-group rounds
+          float x[4][NCB][4];
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            const int row = 32 * wq + 8 * o + ro;
+            const bool rl = (row >> 2) < ne;
+            const float* rs = q + e0 * 4 * Np + (int64_t)row * Np;
+#pragma unroll
+            for (int cb = 0; cb < NCB; ++cb) {
+              const int cg = 4 * cb + cq;
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int n = kc * KC + 4 * cg + j;
+                x[o][cb][j] = (rl && cg < KC / 4 && n < Np) ? rs[n] : 0.f;
+              }
+            }
+          }
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            const int row = 32 * wq + 8 * o + ro;
+#pragma unroll
+            for (int cb = 0; cb < NCB; ++cb) {
+              const int cg = 4 * cb + cq;
+              if (cg >= KC / 4) continue;
+              float h[4], l[4];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) tf32_split(x[o][cb][j], h[j], l[j]);
+              const int off = tc_offset<KC>(row, 4 * cg);
+              *reinterpret_cast<float4*>(Ah + off) = make_float4(h[0], h[1], h[2], h[3]);
+              *reinterpret_cast<float4*>(Al + off) = make_float4(l[0], l[1], l[2], l[3]);
+            }
+          }
+        }
+        if constexpr (!T::BRES) cp_async_wait_all();
+        tc_fence_smem();
+        // the producers' writes of this piece; a stop flag raised anywhere ends every producer
+        ok = !producers_sync_or(*stop != 0u);
+        if (r == 0 && ok) {
+          // the accumulator's previous tile has been read out
+          if (kc == 0 && i >= NACC && !tc_mbar_wait(acc_empty0 + 8 * acc, ((i / NACC) - 1) & 1, kTcWaitPolls)) {
+            *stop = 1u;
+          } else {
+            tc_fence_after();
+            const uint32_t a_hi = smem_addr(Ah), a_lo = smem_addr(Al);
+            const uint32_t b_hi = smem_addr(Bs + (T::BRES ? 0 : slot) * 2 * T::bsz), b_lo = b_hi + T::bsz * 4;
+            // the piece's first K step within the operator's columns (resident: all of them)
+            const uint32_t bk0 = T::BRES ? (uint32_t)kc * (KC / 8) * 256 : 0u;
+            constexpr uint32_t idesc = tc_idesc_tf32(128, T::CN);
+#pragma unroll
+            for (int ch = 0; ch < T::NCH; ++ch) {
+              const uint32_t boff = (uint32_t)ch * T::CN * T::BK * 4 + bk0;  // CN rows of B
+              const uint32_t dcol = tmem + acc * NP + ch * T::CN;
+#pragma unroll
+              for (int st = 0; st < KC / 8; ++st) {
+                const uint64_t ah = tc_smem_desc(a_hi + 256 * st, 128, 32 * KC);
+                const uint64_t al = tc_smem_desc(a_lo + 256 * st, 128, 32 * KC);
+                const uint64_t bh = tc_smem_desc(b_hi + boff + 256 * st, 128, 32 * T::BK);
+                const uint64_t bl = tc_smem_desc(b_lo + boff + 256 * st, 128, 32 * T::BK);
+                tc_mma_tf32(dcol, ah, bh, idesc, kc > 0 || st > 0);
+                tc_mma_tf32(dcol, ah, bl, idesc, true);
+                tc_mma_tf32(dcol, al, bh, idesc, true);
+              }
+            }
+            tc_commit(slot_free0 + 8 * slot);
+            if (kc == NKC - 1) tc_commit(acc_full0 + 8 * acc);
+            last_free = slot_free0 + 8 * slot;
+            last_use = use;
+          }
+        }
+      }
+    }
+    if (r == 0 && last_use >= 0) tc_mbar_wait(last_free, last_use & 1, kTcWaitPolls);  // no MMA left in flight
+  } else {
+    // ---- epilogue: thread tid reads TMEM lane tid (field f of element el of the tile)
     const int el = tid >> 2, f = tid & 3;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-    float* dst = tr + ((e0 + el) * Nfc) * 4 + f;
-#pragma unroll 1
-    for (int c0 = 0; c0 < NP; c0 += 16) {
-      float v[16];
-      tc_ld16(tl + c0, v);
-      tc_wait_ld();
-      if (el < ne) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (c0 + i < Nfc) dst[(c0 + i) * 4] = v[i];
+    int i = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+      const int64_t e0 = tile * EPT;
+      const int ne = (int)min((int64_t)EPT, K - e0);
+      const int acc = i % NACC;
+      if (!tc_mbar_wait(acc_full0 + 8 * acc, (i / NACC) & 1, kTcWaitPolls)) {
+        *stop = 1u;
+        ok = false;
+        break;
       }
+      tc_fence_after();
+      const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16) + acc * NP;
+      float* dst = tr + (e0 + el) * Nfc * 4;
+#pragma unroll 1
+      for (int c0 = 0; c0 < NP; c0 += 16) {
+        float v[16];
+        tc_ld16(tl + c0, v);
+        tc_wait_ld();
+        // 4 x 4 transposes within each quad of lanes (the element's four fields): lane f ends
+        // with the four fields of points c0 + 4 b + f, one 16-byte store each
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          float a[4] = {v[4 * b], v[4 * b + 1], v[4 * b + 2], v[4 * b + 3]};
+          quad_transpose(a, f);
+          const int g = c0 + 4 * b + f;
+          if (el < ne && g < Nfc) *reinterpret_cast<float4*>(dst + 4 * g) = make_float4(a[0], a[1], a[2], a[3]);
+        }
+      }
+      tc_fence_before();
+      tc_mbar_arrive(acc_empty0 + 8 * acc);
     }
-    tc_fence_before();  // these reads precede the next tile's MMAs (issued after a barrier)
   }
-  // a wait that gave up may leave MMAs in flight: wait for the last commit once more, then free
-  if (!ok && tid == 0) {
-    atomicAdd(&g_tc32_timeouts, 1);
-    tc_mbar_wait(mbar, (phase - 1) & 1, kTcWaitPolls);
-  }
+  if (!ok && (tid == 0 || tid == 128)) atomicAdd(&g_tc32_timeouts, 1);
   cp_async_wait_all();
   tc_fence_before();
   __syncthreads();
-  if (tid < 32) tc_dealloc(tmem, T::TCOLS);
+  if (warp == 0) tc_dealloc(tmem, T::TCOLS);
 }
 
 }  // namespace pyrdg

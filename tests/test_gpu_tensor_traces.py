@@ -28,8 +28,7 @@ def torch_cuda():
 def _run(v, e, N, dt, nsteps, traces, mixing=False):
     from paper_1502_07703_gb300.binding import Solver
     with Solver(v, e, N, precision="f32") as s:
-        if traces:
-            s.set_tensor_traces(True)
+        s.set_tensor_traces(traces)  # explicit either way: the default depends on the degree
         if mixing:
             s.set_tensor_mixing(True)
         s.project(0.0)
