@@ -261,8 +261,8 @@ int pyr_dg_set_tensor_mixing(pyr_dg* h, int enable);
  * FP64 from the trace kernel applied to unit states and split on the host. With enable != 0
  * every stage runs the stage kernel without its trace passes, then this kernel writes the
  * new state's traces into the other half of the trace pair; 0 returns to the stage kernel's
- * own traces. FP32 wave handles of at least 40,000 elements start with it at N = 2..6, where
- * it measured faster; smaller meshes and N = 1, 7 start without it. Enabling builds the
+ * own traces. FP32 wave handles of at least 40,000 elements start with it at N = 2..7, where
+ * it measured faster; smaller meshes and N = 1 start without it. Enabling builds the
  * operator once (about 2 Nfc Np floats).
  * FP32 wave handles only, else PYR_DG_ERR_BAD_ARG. Completion waits are bounded as for
  * pyr_dg_set_tensor_mixing. */

@@ -372,8 +372,8 @@ struct Impl {
     l.tctr_np = T32<N>::NP;
     l.tctr_op_floats = T32<N>::op_floats;
     // measured (stage without its trace passes + this kernel, against the stage kernel's own
-    // traces) on 48,000 to 196,608 pyramids: faster at N = 2 to 6, slower at N = 1, level at N = 7
-    l.tctr_default = kTC && N >= 2 && N <= 6;
+    // traces) on 48,000 to 196,608 pyramids: faster at N = 2 to 7, slower at N = 1
+    l.tctr_default = kTC && N >= 2;
     l.nodal_ntr = NodalDims<N>::NTR;
     l.nodal_ntab = NodalDims<N>::size;
     l.nodal_trace = sizeof(T) == 8 ? &nodal_trace : nullptr;

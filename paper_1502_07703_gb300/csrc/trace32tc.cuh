@@ -10,9 +10,9 @@
 //    operand layout (K-major, no swizzle). At N <= 5 the whole map stays in shared memory for
 //    the CTA's lifetime; above that it is cut along K into pieces of 32 modes brought in per tile
 //    (from L2) into two alternating slots. The state side is cut the same way at N >= 5;
-//  - warp-specialised persistent CTAs of 256 threads: warps 4-7 produce (thread r converts row r
-//    of each operand piece from the state into TF32 hi and lo parts, the operator piece arrives
-//    by cp.async, and thread 0 of the group issues the MMAs), warps 0-3 drain the accumulators
+//  - warp-specialised persistent CTAs: PW producer warps from warp 4 on convert the state into
+//    TF32 hi and lo operand pieces (the operator piece arrives by cp.async, and thread 0 of the
+//    group issues the MMAs), warps 0-3 drain the accumulators
 //    (thread t reads TMEM lane t, its row, and stores that field of its element's face points
 //    into the trace layout K x Nfc x 4). Two operand slots and, where TMEM holds them, two
 //    accumulators let the conversion of the next piece and the stores of the previous tile
@@ -29,14 +29,15 @@ __device__ __forceinline__ void tc_mbar_arrive(uint32_t mbar) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
 }
 
-// Barrier of the 128 producer threads (named barrier 1) that also ORs a flag across them, so
-// that every producer takes the same branch after it.
+// Barrier of the producer threads (named barrier 1, nthr of them) that also ORs a flag across
+// them, so that every producer takes the same branch after it.
+template <int nthr>
 __device__ __forceinline__ bool producers_sync_or(bool v) {
   uint32_t out;
   asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
       : "=r"(out)
-      : "r"((uint32_t)v)
+      : "r"((uint32_t)v), "n"(nthr)
       : "memory");
   return out != 0;
 }
@@ -75,7 +76,10 @@ __device__ __forceinline__ void quad_transpose(float (&a)[4], int u) {
 template <int N>
 struct T32 {
   using d = Dims<N>;
-  static constexpr int NT = 256;                        // warps 0-3 drain, 4-7 produce
+  // producer warps (4 .. 4 + PW - 1): more warps cover more of the state loads' latency; 16
+  // measured faster from N = 5 up, 8 below (the MMAs per piece are few there)
+  static constexpr int PW = N >= 5 ? 16 : 8;
+  static constexpr int NT = 128 + 32 * PW;              // warps 0-3 drain the accumulators
   static constexpr int EPT = 32;                        // elements per tile (x 4 fields = M)
   static constexpr int KP = (d::Np + 7) / 8 * 8;        // modes, padded to the TF32 K step
   static constexpr int NP = (d::Nfc + 15) / 16 * 16;    // face points, padded (MMA N step)
@@ -98,10 +102,10 @@ struct T32 {
   static constexpr size_t bars = b0 + NBS * 2 * bsz;    // 6 mbarriers, TMEM address, stop flag
   static constexpr size_t bytes = (bars + 16) * sizeof(float);
   static_assert(bytes <= 227 * 1024, "tensor-core trace kernel shared memory");
-  // resident CTAs per SM: at most 8 of 256 threads, and as many as their TMEM columns fit in
+  // resident CTAs per SM: at most 2048 / NT, and as many as their TMEM columns fit in
   // the SM's 512 (an allocation beyond that would wait for another CTA to exit); the launch
   // asks for enough shared memory that no more than that many fit
-  static constexpr int CTAS_TMEM = 512 / TCOLS < 8 ? 512 / TCOLS : 8;
+  static constexpr int CTAS_TMEM = 512 / TCOLS < 2048 / NT ? 512 / TCOLS : 2048 / NT;
   static constexpr size_t pad_bytes = (228 * 1024) / (CTAS_TMEM + 1) - 1024 + 1024;
   static constexpr size_t launch_bytes = bytes > pad_bytes ? bytes : pad_bytes;
   static constexpr int CTAS_SMEM = (int)((228 * 1024) / (launch_bytes + 1024));
@@ -113,7 +117,7 @@ struct T32 {
 };
 
 template <int N>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(T32<N>::NT, 1)
     trace32tc_kernel(int64_t K, const float* __restrict__ q, float* __restrict__ tr, const float* __restrict__ op) {
   using T = T32<N>;
   using d = Dims<N>;
@@ -143,10 +147,11 @@ __global__ void __launch_bounds__(256, 1)
 
   if (warp >= 4) {
     // ---- producers: operand pieces and the MMAs
-    const int r = tid - 128;  // operand row: field r % 4 of element r / 4 of the tile
+    constexpr int NPT = 32 * T::PW;  // producer threads
+    const int r = tid - 128;         // producer index
     float* Bs = sm + T::b0;
     if constexpr (T::BRES) {  // the operator, once
-      for (int x = r; x < (int)(2 * T::bsz / 4); x += 128) cp_async16(Bs + 4 * x, op + 4 * x);
+      for (int x = r; x < (int)(2 * T::bsz / 4); x += NPT) cp_async16(Bs + 4 * x, op + 4 * x);
       cp_async_commit();
       cp_async_wait_all();
     }
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(256, 1)
       const int acc = i % NACC;
       const int64_t tn = tile + gridDim.x;
       if (tn < ntiles)  // the next tile's state into L2
-        prefetch_l2(q + tn * EPT * 4 * Np, sizeof(float) * 4 * Np * (size_t)min((int64_t)EPT, K - tn * EPT), r, 128);
+        prefetch_l2(q + tn * EPT * 4 * Np, sizeof(float) * 4 * Np * (size_t)min((int64_t)EPT, K - tn * EPT), r, NPT);
       for (int kc = 0; kc < NKC && ok; ++kc, ++pc) {
         const int slot = pc & 1, use = pc >> 1;
         // the slot's previous piece has been multiplied
@@ -169,19 +174,21 @@ __global__ void __launch_bounds__(256, 1)
         if constexpr (!T::BRES) {
           float* Bh = Bs + slot * 2 * T::bsz;
           const float* ps = op + (size_t)kc * 2 * T::bsz;
-          for (int x = r; x < (int)(2 * T::bsz / 4); x += 128) cp_async16(Bh + 4 * x, ps + 4 * x);
+          for (int x = r; x < (int)(2 * T::bsz / 4); x += NPT) cp_async16(Bh + 4 * x, ps + 4 * x);
           cp_async_commit();
         }
-        // operand rows of this piece: lane l of producer warp w takes rows 32 w + 8 o + (l % 8)
-        // and column groups 4 cb + l / 8 (4 modes each), so that each 8-lane store fills one
-        // core matrix; every load of the piece is issued before any conversion
+        // operand rows of this piece: lane l of producer warp w takes rows RW w + 8 o + (l % 8)
+        // (RW = 128 / PW rows per warp) and column groups 4 cb + l / 8 (4 modes each), so that
+        // each 8-lane store fills one core matrix; every load of the piece is issued before any
+        // conversion
         {
+          constexpr int RW = 128 / T::PW, NO = RW / 8;
           const int lane = r & 31, wq = r >> 5, ro = lane & 7, cq = lane >> 3;
           constexpr int NCB = (KC / 4 + 3) / 4;  // column-group rounds
-          float x[4][NCB][4];
+          float x[NO][NCB][4];
 #pragma unroll
-          for (int o = 0; o < 4; ++o) {
-            const int row = 32 * wq + 8 * o + ro;
+          for (int o = 0; o < NO; ++o) {
+            const int row = RW * wq + 8 * o + ro;
             const bool rl = (row >> 2) < ne;
             const float* rs = q + e0 * 4 * Np + (int64_t)row * Np;
 #pragma unroll
@@ -195,8 +202,8 @@ __global__ void __launch_bounds__(256, 1)
             }
           }
 #pragma unroll
-          for (int o = 0; o < 4; ++o) {
-            const int row = 32 * wq + 8 * o + ro;
+          for (int o = 0; o < NO; ++o) {
+            const int row = RW * wq + 8 * o + ro;
 #pragma unroll
             for (int cb = 0; cb < NCB; ++cb) {
               const int cg = 4 * cb + cq;
@@ -213,7 +220,7 @@ __global__ void __launch_bounds__(256, 1)
         if constexpr (!T::BRES) cp_async_wait_all();
         tc_fence_smem();
         // the producers' writes of this piece; a stop flag raised anywhere ends every producer
-        ok = !producers_sync_or(*stop != 0u);
+        ok = !producers_sync_or<NPT>(*stop != 0u);
         if (r == 0 && ok) {
           // the accumulator's previous tile has been read out
           if (kc == 0 && i >= NACC && !tc_mbar_wait(acc_empty0 + 8 * acc, ((i / NACC) - 1) & 1, kTcWaitPolls)) {
