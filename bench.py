@@ -462,10 +462,12 @@ def measure_advection(binding, nx, n, precision, steps, warmup, dev):
     return out
 
 
-def measure_batch(binding, steps, warmup, dev, count=256, alone=True):
+def measure_batch(binding, steps, warmup, dev, count=256, alone=True, mode="auto"):
     """Batching form: `count` independent meshes (sizes log-uniform 48..49,152 pyramids,
     degrees uniform in 2..6, seed 2), FP32, each with its own CFL time step, advanced by
-    one graph-captured batch step per call."""
+    one graph-captured batch step per call. mode: the setup autotuner's launch mode ("auto"),
+    or one forced ("groups": a launch per degree group, "single": one for all), for profiling
+    runs whose timings the profiler distorts."""
     import torch
     from paper_1502_07703_gb300.mesh import batch_mesh_shapes, make_pyramid_mesh
 
@@ -475,6 +477,8 @@ def measure_batch(binding, steps, warmup, dev, count=256, alone=True):
         v, e = make_pyramid_mesh(nx, ny, nz, delta=DELTA, seed=1000 + i)
         meshes.append((v, e, n))
     b = binding.Batch(meshes, precision="f32", device=dev)
+    if mode != "auto":
+        b.set_launch_mode(mode == "single")
     dt = b.dt_cfl(0.5)
     b.project(0.0)
     stream = torch.cuda.ExternalStream(b.stream_ptr, device=dev)
@@ -617,6 +621,8 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="only time the batching form (256 meshes, N = 2..6, FP32) and print it as JSON "
                          "(for profiling runs)")
+    ap.add_argument("--batch-launch-mode", default="auto", choices=["auto", "groups", "single"],
+                    help="with --batch: keep the autotuner's launch mode or force one (for profiling runs)")
     ap.add_argument("--equation", default="wave", choices=["wave", "advection"],
                     help="advection: only time the scalar advection workload (Sec. 4.1) on a periodic "
                          "nx^3 box at --degree and --precision and print that as JSON (for profiling runs)")
@@ -639,7 +645,8 @@ def main():
     device = torch.device("cuda", dev)
     if args.batch:
         if rank == 0:
-            print(json.dumps(measure_batch(binding, args.steps, args.warmup, dev, alone=False)), flush=True)
+            print(json.dumps(measure_batch(binding, args.steps, args.warmup, dev, alone=False,
+                                           mode=args.batch_launch_mode)), flush=True)
         return
     if args.equation == "advection":
         if rank == 0:
