@@ -68,6 +68,19 @@ def test_tensor_traces_several_tiles_per_cta(torch_cuda, N):
     assert rel <= 2e-6, rel
 
 
+@pytest.mark.parametrize("N,nelem", [(2, 1), (5, 1), (7, 1), (3, 33), (6, 33)])
+def test_tensor_traces_ragged_tiles(torch_cuda, N, nelem):
+    """A single pyramid (one tile holding one element) and 33 pyramids (a full tile and one
+    element), 4 steps against the oracle."""
+    v, e = make_pyramid_mesh(3, 2, 1, delta=0.06, seed=60 + N)
+    e = e[:nelem]
+    dg = PyramidDG(v, e, N)
+    dt = dg.dt_cfl(0.5)
+    U_or = dg.lsrk4(dg.project_exact(0.0), dt, 4)
+    tc = _run(v, e, N, dt, 4, True)
+    check(dg, dg.values_phi(tc), dg.values_psi(U_or), TOL["f32"], ("tensor traces, ragged", N, nelem))
+
+
 def test_tensor_traces_with_tensor_mixing(torch_cuda):
     N = 5
     v, e = make_pyramid_mesh(2, 2, 2, delta=0.1, seed=7)
