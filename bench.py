@@ -618,6 +618,9 @@ def main():
     ap.add_argument("--tensor-mixing", action="store_true",
                     help="with --precision f32: the stage kernel with the level mixing on the tensor cores "
                          "(for profiling runs)")
+    ap.add_argument("--tensor-traces", default="auto", choices=["auto", "on", "off"],
+                    help="keep the handle's default trace path or force the tensor-core traces on or off "
+                         "(for profiling runs)")
     ap.add_argument("--batch", action="store_true",
                     help="only time the batching form (256 meshes, N = 2..6, FP32) and print it as JSON "
                          "(for profiling runs)")
@@ -662,6 +665,8 @@ def main():
     s = binding.Solver(v, e, nd, precision=prec, bc="wall", tau=1.0, device=dev, basis=args.basis)
     if args.tensor_mixing:
         s.set_tensor_mixing(True)
+    if args.tensor_traces != "auto":
+        s.set_tensor_traces(args.tensor_traces == "on")
     K, Np = s.K, s.Np
     tb = 8 if prec == "f64" else 4
     dt = s.dt_cfl(0.5)

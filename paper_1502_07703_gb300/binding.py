@@ -332,9 +332,11 @@ class Solver:
         _check(lib().pyr_dg_set_tensor_mixing(self._h, 1 if enable else 0))
 
     def set_tensor_traces(self, enable=True):
-        """FP32 wave handles: interpolate each stage's new state to the face points on the tensor
-        cores (tcgen05 TF32, 3-term split, 32 elements x 4 fields per MMA tile) instead of in the
-        stage kernel."""
+        """Modal wave handles: interpolate each stage's state to the face points on the tensor
+        cores. FP32: tcgen05 TF32, 3-term split, 32 elements x 4 fields per MMA tile, instead of
+        in the stage kernel. FP64 (N = 2..4): exact balanced BF16 slices of the trace map and of
+        the state, 8 elements x 4 fields per tile, FP64-accurate, instead of the FP64 trace
+        kernel."""
         _check(lib().pyr_dg_set_tensor_traces(self._h, 1 if enable else 0))
 
     def set_error_cache(self, enable=True):

@@ -2,6 +2,7 @@
 // (host builder + device geometry), and the per-call launch sequences.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -14,6 +15,7 @@
 
 #include "../../include/pyrdg.h"
 #include "builder.h"
+#include "exact64.h"
 #include "handle.h"
 #include "launch.h"
 
@@ -239,7 +241,7 @@ int enqueue_steps(pyr_dg* h, int nsteps, double dt) {
         CUDA_TRY(prof_end(h, slot));
         if (h->use_tctr) {  // else: the new state's traces on the tensor cores
           CUDA_TRY(prof_begin(h, 0, &slot));
-          h->L->trace32tc(h->K, h->q, buf[1 - h->tr_cur], h->tctr_op, h->tctr_blocks, h->stream);
+          h->L->trace32tc(h->K, h->q, buf[1 - h->tr_cur], (const float*)h->tctr_op, h->tctr_blocks, h->stream);
           CUDA_TRY(prof_end(h, slot));
         }
         h->tr_cur = 1 - h->tr_cur;
@@ -273,7 +275,10 @@ int enqueue_steps(pyr_dg* h, int nsteps, double dt) {
     for (int s = 0; s < 5; ++s) {
       size_t slot = 0;
       CUDA_TRY(prof_begin(h, 0, &slot));
-      h->L->trace(h->K, h->q, h->tab, h->tr, h->stream);
+      if (h->use_tctr)
+        h->L->trace64tc(h->K, h->q, h->tr, h->tctr_op, h->tctr_blocks, h->stream);
+      else
+        h->L->trace(h->K, h->q, h->tab, h->tr, h->stream);
       CUDA_TRY(prof_end(h, slot));
       CUDA_TRY(prof_begin(h, 1, &slot));
       h->L->rhs_update(h->K, h->q, h->res, h->tr, h->mapP, h->geo, h->gface, h->invM, h->tab, h->bc, h->tau, kRkA[s],
@@ -297,10 +302,13 @@ float tf32_round(float x) {
   return y;
 }
 
-// Operand of the tensor-core trace kernel: the dense trace map Phi_f (mode n at face point g)
+// Operand of the tensor-core trace kernels: the dense trace map Phi_f (mode n at face point g)
 // in FP64, obtained by applying the FP64 trace kernel to the Np unit states (pseudo-element n
-// holds mode n in every field), split into TF32 hi and lo parts and laid out in NKC pieces of
-// KC mode columns, each NP x KC (rows = face points) in the K-major no-swizzle operand layout.
+// holds mode n in every field). FP32 handles: split into TF32 hi and lo parts and laid out in
+// NKC pieces of KC mode columns, each NP x KC (rows = face points) in the K-major no-swizzle
+// operand layout. FP64 handles: each face point's row cut into 8 exact balanced BF16 digits
+// against the row's largest exponent, slice by slice 128 x KP in the operand layout (core
+// matrices of 8 rows x 8 BF16), then the 128 row exponents.
 int build_trace_operator(pyr_dg* h) {
   const pyrdg::Launchers* L64 = pyrdg::get_launchers(h->N, 0);
   if (!L64) return fail(PYR_DG_ERR_UNSUPPORTED_N, "no FP64 launchers for N = %d", h->N);
@@ -326,6 +334,31 @@ int build_trace_operator(pyr_dg* h) {
   cudaFree(dq);
   cudaFree(dtr);
   if (e != cudaSuccess) return fail(PYR_DG_ERR_CUDA, "tensor-core traces: trace map: %s", cudaGetErrorString(e));
+  if (!h->use_stage32) {  // FP64
+    const int KP = h->L->tctr64_kp;
+    std::vector<unsigned char> op(h->L->tctr64_op_bytes, 0);
+    uint16_t* A = reinterpret_cast<uint16_t*>(op.data());
+    int32_t* Fx = reinterpret_cast<int32_t*>(op.data() + (size_t)8 * 128 * KP * 2);
+    for (int g = 0; g < Nfc; ++g) {
+      int F = 0;
+      for (int n = 0; n < Np; ++n) F = std::max(F, pyrdg::ex64_exp(tr[((size_t)n * Nfc + g) * 4]));
+      Fx[g] = F;
+      for (int n = 0; n < Np; ++n) {
+        int32_t a[8];
+        pyrdg::ex64_slices(tr[((size_t)n * Nfc + g) * 4], F, a);
+        for (int j = 0; j < 8; ++j) {
+          const float v = (float)a[j];  // at most 8 significant bits: exact in BF16
+          uint32_t b;
+          std::memcpy(&b, &v, 4);
+          A[(size_t)j * 128 * KP + (size_t)(g >> 3) * (8 * KP) + (n >> 3) * 64 + (g & 7) * 8 + (n & 7)] =
+              (uint16_t)(b >> 16);
+        }
+      }
+    }
+    CUDA_TRY(cudaMalloc(&h->tctr_op, op.size()));
+    CUDA_TRY(cudaMemcpy(h->tctr_op, op.data(), op.size(), cudaMemcpyHostToDevice));
+    return PYR_DG_OK;
+  }
   const int KC = h->L->tctr_kc, NKC = h->L->tctr_nkc, NP = h->L->tctr_np;
   std::vector<float> op(h->L->tctr_op_floats, 0.f);
   for (int kc = 0; kc < NKC; ++kc) {
@@ -356,6 +389,11 @@ int enable_tensor_traces(pyr_dg* h) {
   }
   int nsm = 1;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  if (!h->use_stage32) {  // FP64: tiles of 8 elements, one CTA per SM
+    h->tctr_blocks = (int)std::min<int64_t>((h->K + 7) / 8, (int64_t)nsm);
+    h->use_tctr = true;
+    return PYR_DG_OK;
+  }
   const int64_t tiles = (h->K + 31) / 32;
   h->tctr_blocks = (int)std::min<int64_t>(tiles, (int64_t)nsm * h->L->blocks_per_sm_trace32tc());
   h->use_tctr = true;
@@ -659,8 +697,8 @@ int pyr_dg_setup(const double* vertices, int64_t Nv, const int32_t* EToV, int64_
   // FP32 wave handles: the new state's face traces on the tensor cores where that is faster,
   // at the degrees the launchers mark and on meshes of at least 40,000 pyramids (measured: from
   // about 8 tiles of 32 elements per SM up the second launch per stage pays for itself)
-  if (h->use_stage32 && h->equation == PYR_DG_WAVE && h->basis == PYR_DG_MODAL && h->L->tctr_default &&
-      h->K >= 40000) {
+  if (h->equation == PYR_DG_WAVE && h->basis == PYR_DG_MODAL && h->K >= 40000 &&
+      (h->use_stage32 ? h->L->tctr_default != 0 : (h->L->tctr64_default != 0 && h->L->trace64tc != nullptr))) {
     const int rc = enable_tensor_traces(h);
     if (rc != PYR_DG_OK) {
       free_all(h);
@@ -1016,8 +1054,10 @@ int pyr_dg_set_tensor_traces(pyr_dg* h, int enable) {
     h->use_tctr = false;
     return PYR_DG_OK;
   }
-  if (!h->use_stage32 || h->equation != PYR_DG_WAVE || h->basis != PYR_DG_MODAL || !h->L->trace32tc)
-    return fail(PYR_DG_ERR_BAD_ARG, "tensor-core traces need an FP32 wave handle");
+  if (h->equation != PYR_DG_WAVE || h->basis != PYR_DG_MODAL ||
+      !(h->use_stage32 ? h->L->trace32tc != nullptr : h->L->trace64tc != nullptr))
+    return fail(PYR_DG_ERR_BAD_ARG,
+                "tensor-core traces need a modal wave handle (FP32, or FP64 with N = 2..4)");
   DeviceGuard g(h->device);
   CUDA_TRY(g.err);
   return enable_tensor_traces(h);

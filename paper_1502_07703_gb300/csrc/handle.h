@@ -38,8 +38,9 @@ struct pyr_dg {
   int tr_cur = 0;
   bool tr_valid = false;
   bool use_tc = false;          // FP32 stage with the tensor-core level mixing (pyr_dg_set_tensor_mixing)
-  bool use_tctr = false;        // FP32 traces on the tensor cores (pyr_dg_set_tensor_traces)
-  float* tctr_op = nullptr;     // their operator (the trace map's TF32 hi/lo parts)
+  bool use_tctr = false;        // traces on the tensor cores (pyr_dg_set_tensor_traces)
+  void* tctr_op = nullptr;      // their operator (FP32: the trace map's TF32 hi/lo parts;
+                                // FP64: its exact BF16 slices and row exponents)
   int tctr_blocks = 0;          // their persistent grid
   int stage_blocks = 0;         // persistent grid of the FP32 stage kernel
   int stage_epb = 1;            // elements per CTA of the FP32 stage kernel

@@ -3,6 +3,7 @@
 #include "dg_kernels.cuh"
 #include "stage32.cuh"
 #include "trace32tc.cuh"
+#include "trace64tc.cuh"
 #include "adv32.cuh"
 #include "adv_kernels.cuh"
 #include "launch.h"
@@ -52,6 +53,11 @@ struct Impl {
     e = cudaFuncSetAttribute(exact_proj_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)ProjQSmem<N>::bytes);
     if (e != cudaSuccess) return e;
+    if constexpr (sizeof(T) == 8 && T64<N>::OK) {
+      e = cudaFuncSetAttribute(trace64tc_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)T64<N>::launch_bytes);
+      if (e != cudaSuccess) return e;
+    }
     if constexpr (sizeof(T) == 8) {
       static_assert(NodalSmem<N>::bytes <= kMaxSmem, "nodal stage kernel shared memory");
       e = cudaFuncSetAttribute(nodal_rhs_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -220,12 +226,17 @@ struct Impl {
     }
     return 0;
   }
+  // FP64 face traces on the tensor cores with FP64 accuracy (exact BF16 slices, T64<N>); one
+  // CTA per SM, over tiles of 8 elements.
+  static void trace64tc(int64_t K, const void* q, void* tr, const void* op, int nblocks, cudaStream_t s) {
+    if constexpr (sizeof(T) == 8 && T64<N>::OK)
+      trace64tc_kernel<N><<<nblocks, T64<N>::NT, T64<N>::launch_bytes, s>>>(
+          K, (const double*)q, (double*)tr, (const unsigned char*)op);
+  }
   static int tc32_timeouts() {
     int n = 0, zero = 0;
-    if constexpr (kTC) {
-      if (cudaMemcpyFromSymbol(&n, g_tc32_timeouts, sizeof(int)) != cudaSuccess) return -1;
-      if (n != 0 && cudaMemcpyToSymbol(g_tc32_timeouts, &zero, sizeof(int)) != cudaSuccess) return -1;
-    }
+    if (cudaMemcpyFromSymbol(&n, g_tc32_timeouts, sizeof(int)) != cudaSuccess) return -1;
+    if (n != 0 && cudaMemcpyToSymbol(g_tc32_timeouts, &zero, sizeof(int)) != cudaSuccess) return -1;
     return n;
   }
   // epb must be one blocks_per_sm32 reports as built (nonzero)
@@ -364,7 +375,7 @@ struct Impl {
     l.error1 = &error1;
     l.stage32tc = kTC ? &stage32tc : nullptr;
     l.blocks_per_sm32tc = kTC ? &blocks_per_sm32tc : nullptr;
-    l.tc32_timeouts = kTC ? &tc32_timeouts : nullptr;
+    l.tc32_timeouts = (kTC || T64<N>::OK) ? &tc32_timeouts : nullptr;
     l.trace32tc = kTC ? &trace32tc : nullptr;
     l.blocks_per_sm_trace32tc = kTC ? &blocks_per_sm_trace32tc : nullptr;
     l.tctr_kc = T32<N>::BK;
@@ -374,6 +385,11 @@ struct Impl {
     // measured (stage without its trace passes + this kernel, against the stage kernel's own
     // traces) on 48,000 to 196,608 pyramids: faster at N = 2 to 7, slower at N = 1
     l.tctr_default = kTC && N >= 2;
+    const bool k64 = sizeof(T) == 8 && T64<N>::OK;
+    l.trace64tc = k64 ? &trace64tc : nullptr;
+    l.tctr64_kp = T64<N>::KP;
+    l.tctr64_op_bytes = T64<N>::op_bytes;
+    l.tctr64_default = 0;
     l.nodal_ntr = NodalDims<N>::NTR;
     l.nodal_ntab = NodalDims<N>::size;
     l.nodal_trace = sizeof(T) == 8 ? &nodal_trace : nullptr;

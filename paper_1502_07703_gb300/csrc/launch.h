@@ -89,6 +89,14 @@ struct Launchers {
   int tctr_kc, tctr_nkc, tctr_np;
   int tctr_default;  // FP32 wave handles start with these traces (measured faster at this degree)
   size_t tctr_op_floats;
+  // FP64 face traces on the tensor cores with FP64 accuracy (null for float and where Nfc > 128
+  // or Np > 102). op: the trace map's 8 exact BF16 slices, each 128 x tctr64_kp (face points x
+  // padded modes) in the K-major no-swizzle operand layout (core matrices of 8 rows x 8
+  // columns), then 128 int32 row exponents; tctr64_op_bytes in all. One CTA per SM.
+  void (*trace64tc)(int64_t K, const void* q, void* tr, const void* op, int nblocks, cudaStream_t s);
+  int tctr64_kp;
+  size_t tctr64_op_bytes;
+  int tctr64_default;  // FP64 wave handles start with these traces
   int nodal_ntr;      // trace points per element of the nodal variant
   int nodal_ntab;     // doubles in its table
 };
