@@ -70,14 +70,13 @@ EX64_HD int ex64_exp(double x) { return (int)((ex64_bits(x) >> 52) & 0x7FF); }
 // Digit offset C = sum_{i=1..7} 64 * 2^(56-7i).
 #define EX64_BALANCE 0x81020408102000ull
 
-// X = trunc(|x| 2^(1085-E)) (E >= the biased exponent of x; 0 for zeros and subnormals).
+// X = trunc(|x| 2^(1085-E)) = (m 2^10) >> (E - e) for the 53-bit significand m and biased
+// exponent e <= E of x (0 for zeros and subnormals).
 EX64_HD uint64_t ex64_fixed(uint64_t bits, int E) {
   const int e = (int)((bits >> 52) & 0x7FF);
-  if (e == 0) return 0;
-  const uint64_t m = (bits & ((1ull << 52) - 1)) | (1ull << 52);
-  const int sh = e - E + 10;  // X = m 2^(e - E + 10)
-  if (sh >= 0) return m << sh;
-  return sh > -64 ? m >> (-sh) : 0;
+  const uint64_t m = e ? ((bits & ((1ull << 52) - 1)) | (1ull << 52)) << 10 : 0;
+  const int sh = E - e;
+  return sh < 64 ? m >> sh : 0;
 }
 
 // The eight signed balanced slices of x against the row exponent E.
@@ -124,6 +123,30 @@ EX64_HD double ex64_combine(const int32_t G[8], int Z) {
   if (bexp <= 0) return 0.0;
   if (bexp >= 2047) return ex64_from_bits(((uint64_t)neg << 63) | (0x7FFull << 52));
   return ex64_from_bits(((uint64_t)neg << 63) | ((uint64_t)bexp << 52) | (mant & ((1ull << 52) - 1)));
+}
+
+// The same sum to FP64 through floor(V / 2^8), which fits in 63 bits when |G_0| < 2^21 (K <= 127
+// terms) and |G_s| < 2^22: one 64-bit integer, rounded once to nearest (ties to even) and scaled
+// by 2^(Z+8). The result is within 2^(Z+8) plus half an ulp of V 2^Z, below the truncation of
+// the dropped levels for K >= 1 (2^(Z+8) = 2^-55 of the scale 2^(E+F-2044)); about half the
+// integer operations of ex64_combine.
+EX64_HD double ex64_combine_fast(const int32_t G[8], int Z) {
+  const int64_t v = (int64_t)G[0] * (1ll << 41) + (int64_t)G[1] * (1ll << 34) + (int64_t)G[2] * (1ll << 27) +
+                    (int64_t)G[3] * (1ll << 20) + (int64_t)G[4] * (1ll << 13) + (int64_t)G[5] * 64 +
+                    (((int64_t)G[6] * 128 + G[7]) >> 8);
+  const uint64_t sgn = (uint64_t)(v >> 63);  // 0 or all ones
+  uint64_t m = ((uint64_t)v ^ sgn) - sgn;    // |v|
+  if (m == 0) return 0.0;
+  const int lz = ex64_clz64(m);
+  m <<= lz;                         // leading one at bit 63
+  uint64_t mant = m >> 11;          // 53 bits, leading one at bit 52
+  const uint64_t rest = m & 0x7FF;  // round bit 10 and sticky bits
+  mant += (rest > 0x400 || (rest == 0x400 && (mant & 1))) ? 1 : 0;
+  const int bexp = 63 - lz + Z + 8 + 1023;  // biased exponent of |v| 2^(Z+8)
+  if (bexp <= 0) return 0.0;
+  if (bexp >= 2047) return ex64_from_bits((sgn << 63) | (0x7FFull << 52));
+  // the leading one adds 1 to the exponent field; a rounding carry to 2^53 adds one more
+  return ex64_from_bits((sgn << 63) | (((uint64_t)(bexp - 1) << 52) + mant));
 }
 
 #if defined(__cplusplus)

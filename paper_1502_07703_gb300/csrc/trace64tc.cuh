@@ -4,8 +4,9 @@
 // balanced BF16 digits against a per-row exponent (exact64.h): Phi_f's rows (face points) once
 // on the host, the state's rows (element-field pairs) per tile here. The level sums
 // G_s = sum_{i+j=s} a_i b_j^T, s = 0..7, are integers below 2^22, exact in FP32 accumulators, and
-// the epilogue recombines them with integer operations into the correctly rounded FP64 value of
-// sum_s G_s 2^(-7s) times the two rows' scales.
+// the epilogue recombines them with integer operations into an FP64 value of sum_s G_s 2^(-7s)
+// times the two rows' scales (ex64_combine_fast: within 2^-55 of the scales' product plus half
+// an ulp).
 //  - tcgen05.mma kind::f16 (BF16 operands, FP32 accumulation in TMEM), M = 128 face points
 //    (Nfc <= 128 for N <= 4), K = the Np modes padded to 16, 32 state rows per tile (8 elements
 //    x 4 fields, the state's own row order). The accumulator of a tile is 8 levels x 32 columns;
@@ -19,10 +20,10 @@
 //    they slice the current one (lane l of producer warp w takes state row 8 w + l % 8 and mode
 //    groups l / 8 + 4 t of 8 modes, so that each 8-lane phase of a slice store fills one core
 //    matrix); the row's exponent is a maximum over the 4 lanes that hold the row; thread 0 of
-//    the group issues the MMAs. Warps 0-7 drain the accumulators (warp w reads TMEM lane
-//    quarter w % 4, i.e. face points 32 (w % 4) + lane, and columns 16 (w / 4) .. + 15, i.e.
-//    elements 4 (w / 4) .. + 3 of the tile) and store the four fields of a face point as 32
-//    contiguous bytes of the trace layout K x Nfc x 4.
+//    the group issues the MMAs. Warps 0 .. EW-1 drain the accumulators (warp w reads TMEM lane
+//    quarter w % 4, i.e. face points 32 (w % 4) + lane, and the CPW = 128 / EW columns from
+//    CPW (w / 4), i.e. CPW / 4 elements of the tile) and store the four fields of a face point
+//    as 32 contiguous bytes of the trace layout K x Nfc x 4.
 // Every wait is bounded like the other tensor-core kernels'; a wait that gives up is counted in
 // g_tc32_timeouts, and the CTA stops (its remaining tiles are left unwritten).
 #pragma once
@@ -63,7 +64,8 @@ struct T64 {
   static constexpr int GPT = (NG + 3) / 4;            // groups per producer thread
   static constexpr int CW = 32;                       // state rows per tile (8 elements x 4 fields)
   static constexpr int EPT = CW / 4;
-  static constexpr int EW = 8, PW = 4;  // epilogue warps (two per TMEM lane quarter), producer warps
+  static constexpr int EW = 8, PW = 4;  // epilogue warps (EW / 4 per TMEM lane quarter), producer warps
+  static_assert(EW % 4 == 0 && (4 * CW / EW) % 8 == 0, "epilogue warps: whole lane quarters, 8-column chunks");
   static constexpr int NT = 32 * (EW + PW);
   static constexpr uint32_t TCOLS = 512;  // two accumulators of 8 levels x 32 columns
   // shared memory (bytes): operator slices, two state slots, 4 exponent rows, mbarriers
@@ -218,8 +220,9 @@ __global__ void __launch_bounds__(T64<N>::NT, 1)
     }
     if (r == 0 && last_use >= 0) tc_mbar_wait(last_free, last_use & 1, kTcWaitPolls);  // no MMA left in flight
   } else {
-    // ---- epilogue: face point g = TMEM lane, 16 state columns (4 elements) per warp
-    const int quarter = warp & 3, half = warp >> 2;
+    // ---- epilogue: face point g = TMEM lane, CPW state columns (CPW / 4 elements) per warp
+    constexpr int CPW = 4 * CW / T::EW, NCC = CPW / 8;
+    const int quarter = warp & 3, part = warp >> 2;
     const int g = 32 * quarter + lane;
     const int F = reinterpret_cast<const int*>(op + 8 * T::asz)[g];
     int i = 0;
@@ -233,23 +236,23 @@ __global__ void __launch_bounds__(T64<N>::NT, 1)
         break;
       }
       tc_fence_after();
-      int Z[16];  // scale exponents of this thread's 16 outputs
+      int Z[CPW];  // scale exponents of this thread's outputs
 #pragma unroll
-      for (int c = 0; c < 16; ++c) Z[c] = Erow[(i & 3) * CW + 16 * half + c] + F - 2107;
-      const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16) + 256u * acc + 16 * half;
+      for (int c = 0; c < CPW; ++c) Z[c] = Erow[(i & 3) * CW + CPW * part + c] + F - 2107;
+      const uint32_t tl = tmem + ((uint32_t)(32 * quarter) << 16) + 256u * acc + CPW * part;
 #pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
+      for (int cc = 0; cc < NCC; ++cc) {
         float v[8][8];  // level s, column 8 cc + k
 #pragma unroll
         for (int s = 0; s < 8; ++s) tc_ld8(tl + 32 * s + 8 * cc, v[s]);
         tc_wait_ld();
-        if (cc == 1) {  // the accumulator is free for the tile after next
+        if (cc == NCC - 1) {  // the accumulator is free for the tile after next
           tc_fence_before();
           tc_mbar_arrive(acc_empty0 + 8 * acc);
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int e = 4 * half + 2 * cc + h;  // element of the tile
+          const int e = (CPW * part + 8 * cc) / 4 + h;  // element of the tile
           double o[4];
 #pragma unroll
           for (int f = 0; f < 4; ++f) {
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(T64<N>::NT, 1)
 #pragma unroll
             for (int s = 0; s < 8; ++s)  // |G_s| < 2^22: the integer sits in the low mantissa bits
               G[s] = (int32_t)__float_as_uint(v[s][4 * h + f] + 12582912.f) - 0x4B400000;
-            o[f] = ex64_combine(G, Z[8 * cc + 4 * h + f]);
+            o[f] = ex64_combine_fast(G, Z[8 * cc + 4 * h + f]);
           }
           if (e < ne && g < Nfc) {
             double2* dst = reinterpret_cast<double2*>(tr + ((e0 + e) * Nfc + g) * 4);

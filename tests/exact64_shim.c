@@ -11,9 +11,12 @@ void shim_slices(const double* x, int n, int E, int32_t* a) {
 
 double shim_combine(const int32_t* G, int Z) { return ex64_combine(G, Z); }
 
+double shim_combine_fast(const int32_t* G, int Z) { return ex64_combine_fast(G, Z); }
+
 /* sum_n x_n y_n through the slices: E, F are the largest biased exponents of x and y; G (8
- * int64) receives the exact level sums; returns the recombined result. */
-double shim_dot(const double* x, const double* y, int K, int64_t* G, int* EF) {
+ * int64) receives the exact level sums; returns the recombined result (ex64_combine_fast if
+ * fast, else ex64_combine). */
+double shim_dot(const double* x, const double* y, int K, int64_t* G, int* EF, int fast) {
   int E = 0, F = 0;
   for (int n = 0; n < K; ++n) {
     if (ex64_exp(x[n]) > E) E = ex64_exp(x[n]);
@@ -31,5 +34,5 @@ double shim_dot(const double* x, const double* y, int K, int64_t* G, int* EF) {
   for (int s = 0; s < 8; ++s) G32[s] = (int32_t)G[s];
   EF[0] = E;
   EF[1] = F;
-  return ex64_combine(G32, E + F - 2107);
+  return fast ? ex64_combine_fast(G32, E + F - 2107) : ex64_combine(G32, E + F - 2107);
 }

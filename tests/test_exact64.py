@@ -5,9 +5,11 @@ built for the host and checked against exact rational arithmetic (fractions.Frac
   in their digit ranges;
 - the recombination of level sums is the correctly rounded FP64 value (ties to even), bit for
   bit, including ties, carries out of the mantissa, negative and zero sums;
+- the fast recombination (floor(V / 2^8) rounded once) stays within its bound;
 - a dot product through the slices stays within the stated error bound of the exact dot
-  product, and its level sums stay below 2^22 (so FP32 accumulation and the magic-number
-  conversion are exact) up to K = 102 terms, also for the largest possible digits."""
+  product, with either recombination, and its level sums stay below 2^22 (so FP32
+  accumulation and the magic-number conversion are exact) up to K = 102 terms, also for the
+  largest possible digits."""
 
 import ctypes
 import os
@@ -36,7 +38,9 @@ def lib(tmp_path_factory):
     L.shim_slices.argtypes = [dp, ctypes.c_int, ctypes.c_int, ip]
     L.shim_combine.argtypes = [ip, ctypes.c_int]
     L.shim_combine.restype = ctypes.c_double
-    L.shim_dot.argtypes = [dp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ip]
+    L.shim_combine_fast.argtypes = [ip, ctypes.c_int]
+    L.shim_combine_fast.restype = ctypes.c_double
+    L.shim_dot.argtypes = [dp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ip, ctypes.c_int]
     L.shim_dot.restype = ctypes.c_double
     return L
 
@@ -127,18 +131,41 @@ def test_combine_is_correctly_rounded(lib):
         assert np.float64(got).view(np.uint64) == np.float64(want).view(np.uint64), (G, Z, got, want)
 
 
-def _dot(lib, x, y):
+def test_fast_combine_within_its_bound(lib):
+    """floor(V / 2^8) rounded once: within 2^(Z+8) plus half an ulp of V 2^Z; exact where V is a
+    multiple of 2^8 with at most 53 significant bits; zero for zero level sums."""
+    rng = np.random.default_rng(6)
+    cases = []
+    for _ in range(3000):
+        G = [int(rng.integers(-(2 ** 21) + 1, 2 ** 21))] + [int(v) for v in rng.integers(-(2 ** 22) + 1, 2 ** 22, 7)]
+        cases.append((G, int(rng.integers(-900, 900))))
+    for t in range(8, 30):  # small sums: few significant bits, and cancellations across levels
+        cases.append((_g_from_v(3 << t), -20))
+        cases.append((_g_from_v(-(5 << t)), 40))
+    for G, Z in cases:
+        V = sum(G[s] * 2 ** (7 * (7 - s)) for s in range(8))
+        got = lib.shim_combine_fast(_ptr(np.array(G, dtype=np.int32), ctypes.c_int32), Z)
+        exact = Fraction(V) * Fraction(2) ** Z
+        half_ulp = Fraction(abs(got)) * Fraction(2) ** -53
+        assert abs(Fraction(got) - exact) <= Fraction(2) ** (Z + 8) + half_ulp, (G, Z)
+        if V % 256 == 0 and abs(V) < 2 ** 61 and (abs(V) >> 8).bit_length() <= 53:
+            assert got == float(exact), (G, Z)
+    assert lib.shim_combine_fast(_ptr(np.zeros(8, dtype=np.int32), ctypes.c_int32), 5) == 0.0
+
+
+def _dot(lib, x, y, fast=0):
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
     G = np.zeros(8, dtype=np.int64)
     EF = np.zeros(2, dtype=np.int32)
     r = lib.shim_dot(_ptr(x, ctypes.c_double), _ptr(y, ctypes.c_double), len(x), _ptr(G, ctypes.c_int64),
-                     _ptr(EF, ctypes.c_int32))
+                     _ptr(EF, ctypes.c_int32), fast)
     return r, G, int(EF[0]), int(EF[1])
 
 
+@pytest.mark.parametrize("fast", [0, 1])
 @pytest.mark.parametrize("K", [1, 5, 14, 30, 55, 91, 102])
-def test_dot_within_bound_and_level_sums_exact_in_fp32(lib, K):
+def test_dot_within_bound_and_level_sums_exact_in_fp32(lib, K, fast):
     rng = np.random.default_rng(K)
     for trial in range(40):
         if trial % 4 == 0:  # modal coefficients: decaying magnitudes, mixed signs
@@ -153,12 +180,14 @@ def test_dot_within_bound_and_level_sums_exact_in_fp32(lib, K):
         if trial % 4 == 2 and K > 1:
             y[-1] = 0.0
             y[-1] = -float(np.dot(x[:-1], y[:-1])) / x[-1]
-        r, G, E, F = _dot(lib, x, y)
+        r, G, E, F = _dot(lib, x, y, fast)
         bounds = [K * 16384] + [K * 4096 * (s + 3) for s in range(1, 8)]
         assert all(abs(int(G[s])) <= bounds[s] for s in range(8)), (G, bounds)
         assert np.all(np.abs(G) < 2 ** 22)
         exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(x, y))
         scale = Fraction(2) ** (E + F - 2044)
         half_ulp = Fraction(abs(r)) * Fraction(2) ** -53 if r != 0 else 0
-        bound = Fraction(151, 10) * K * Fraction(2) ** -58 * scale + half_ulp
+        # inputs truncated (2 K 2^-56), levels 8..14 dropped (7.1 K 2^-58), the fast form's
+        # floor (2^-55, of the scale 2^(E+F-2044)), the final rounding
+        bound = (Fraction(151, 10) * K * Fraction(2) ** -58 + fast * Fraction(2) ** -55) * scale + half_ulp
         assert abs(Fraction(r) - exact) <= bound, (K, trial, float(abs(Fraction(r) - exact) / scale))
