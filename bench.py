@@ -719,6 +719,40 @@ def main():
                 "kernel_ms_avg": rhs_ms / rhs_n, "trace_kernel_ms_avg": tr_ms / tr_n if tr_n else 0.0,
                 "kernel_share": rhs_ms / (rhs_ms + tr_ms)}
 
+    # ---- the face traces: which path the step ran (the handle's default unless forced), that
+    # kernel's algorithmic bandwidth, and the step with the other path
+    traces = {"tensor_traces": s.tensor_traces, "kernel_ms_avg": tr_ms / tr_n if tr_n else 0.0}
+    if prec == "f64" and args.basis == "modal" and tr_n:
+        tb = 8 * 4 * (Np + s.Nfc)  # state read, traces written
+        gbs = tb * K / (tr_ms / tr_n * 1e-3) / 1e9
+        traces.update({"kernel": f"trace64tc_kernel<{nd}>" if traces["tensor_traces"] else f"trace_kernel<{nd},double>",
+                       "bytes_per_element": tb, "achieved_gbs": gbs, "hbm_peak_gbs": HBM_GBS,
+                       "hbm_peak_kind": HBM_KIND, "hbm_frac": gbs / HBM_GBS})
+        try:
+            s.set_tensor_traces(not traces["tensor_traces"])
+            other = True
+        except binding.PyrDGError:
+            other = False  # no tensor-core traces for this handle
+        if other:
+            for _ in range(2):
+                s.step(1, dt)
+            s.sync()
+            s.profile(True)
+            ev0.record(stream)
+            for _ in range(args.steps):
+                s.step(1, dt)
+            ev1.record(stream)
+            torch.cuda.synchronize(device)
+            s.sync()
+            o_ms = ev0.elapsed_time(ev1) / args.steps
+            p2 = s.profile_read()
+            s.profile(False)
+            s.set_tensor_traces(traces["tensor_traces"])
+            traces["other_trace_path"] = {
+                "tensor_traces": not traces["tensor_traces"], "ms_per_step": o_ms,
+                "trace_kernel_ms_avg": p2["trace"][0] / p2["trace"][1],
+                "value": dofs_per_stage * 5 / (o_ms * 1e-3)}
+
     # ---- end to end through the public API with host buffers (state at t = 0 re-sent every step)
     s.project(0.0)
     U0 = s.get_state()
@@ -784,6 +818,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": rhs_n + tr_n,
         "roofline": roofline,
+        "face_traces": traces,
         "cpu_baseline": cpu,
         "l2_error_vs_exact": {"abs": err_abs, "rel": err_rel},
         "precision_forms": forms,

@@ -252,21 +252,37 @@ int pyr_dg_time(const pyr_dg* h, double* t);
  * PYR_DG_ERR_TIMEOUT if one gave up since the last check. */
 int pyr_dg_set_tensor_mixing(pyr_dg* h, int enable);
 
-/* FP32 face traces on the tensor cores (Alg. 3's interpolation of the updated state to the
- * face points, batched over elements). The trace map Phi_f (mode n at face point g, Nfc x Np)
- * is the same for every element and field, so the traces of 32 elements are one product
- * T = U Phi_f^T of M = 128 rows (element x field, the state's own layout), K = Np modes,
- * N = Nfc points: tcgen05.mma kind::tf32 with the 3-term split A_hi B_hi + A_hi B_lo +
- * A_lo B_hi (about FP32 accuracy), FP32 accumulation in tensor memory. Phi_f is taken in
- * FP64 from the trace kernel applied to unit states and split on the host. With enable != 0
- * every stage runs the stage kernel without its trace passes, then this kernel writes the
- * new state's traces into the other half of the trace pair; 0 returns to the stage kernel's
- * own traces. FP32 wave handles of at least 40,000 elements start with it at N = 2..7, where
- * it measured faster; smaller meshes and N = 1 start without it. Enabling builds the
- * operator once (about 2 Nfc Np floats).
- * FP32 wave handles only, else PYR_DG_ERR_BAD_ARG. Completion waits are bounded as for
- * pyr_dg_set_tensor_mixing. */
+/* Face traces on the tensor cores (Alg. 3's interpolation of the state to the face points,
+ * batched over elements), for the stepping of modal wave handles (pyr_dg_step). The trace map
+ * Phi_f (mode n at face point g, Nfc x Np) is the same for every element and field, so the
+ * traces of a tile of elements are one product with the state's rows (element x field, the
+ * state's own layout) and K = Np modes. Phi_f is taken in FP64 from the trace kernel applied
+ * to unit states and prepared on the host when the traces are first enabled.
+ *  - FP32 handles: T = U Phi_f^T over 32 elements (M = 128 rows), tcgen05.mma kind::tf32 with
+ *    the 3-term split A_hi B_hi + A_hi B_lo + A_lo B_hi (about FP32 accuracy), FP32
+ *    accumulation in tensor memory. Every stage runs the stage kernel without its trace passes,
+ *    then this kernel writes the new state's traces into the other half of the trace pair.
+ *    Handles of at least 40,000 elements start with it at N = 2..7, where it measured faster;
+ *    smaller meshes and N = 1 start without it. The operator takes about 2 Nfc Np floats.
+ *  - FP64 handles at N = 2..4 (Nfc <= 128 face points, Np <= 102 modes): Phi_f U^T over 8
+ *    elements with FP64 accuracy: Phi_f's rows and the state's rows are cut into 8 exact
+ *    balanced base-128 digits against each row's largest exponent (BF16 operands of
+ *    tcgen05.mma kind::f16), the 36 digit products of each level s = i + j <= 7 are summed
+ *    exactly as integers below 2^22 in FP32 accumulators, and integer arithmetic recombines
+ *    the 8 levels into FP64. Each trace is within 15.1 K 2^-58 + 2^-55 of 2^(E+F-2044) (E, F:
+ *    the two rows' largest biased exponents, K = Np terms) plus half an ulp of the exact dot
+ *    product, below FP64's own worst-case rounding bound for such a sum. It replaces the FP64
+ *    trace kernel before each fused stage; pyr_dg_rhs and the projection keep that kernel.
+ *    Handles of at least 40,000 elements start with it where it measured faster (N = 4). The
+ *    operator takes 16 * 128 * Np(padded to 16) bytes.
+ * enable != 0 selects these traces, 0 the CUDA-core paths. Other handles (advection, the nodal
+ * basis, FP64 at N = 1 or N >= 5) return PYR_DG_ERR_BAD_ARG. Completion waits are bounded as
+ * for pyr_dg_set_tensor_mixing. */
 int pyr_dg_set_tensor_traces(pyr_dg* h, int enable);
+
+/* Whether the handle's stepping currently computes the face traces on the tensor cores
+ * (pyr_dg_set_tensor_traces or the handle's default): *enabled = 1 or 0. */
+int pyr_dg_get_tensor_traces(const pyr_dg* h, int* enabled);
 
 /* Wait for all work enqueued by this handle, staged state copies included. */
 int pyr_dg_sync(pyr_dg* h);

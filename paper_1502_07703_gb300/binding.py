@@ -98,6 +98,7 @@ _SIGNATURES = {
     "pyr_dg_host_nodal_points": (ctypes.c_int, [ctypes.c_int, _c_dp]),
     "pyr_dg_set_tensor_mixing": (ctypes.c_int, [_c_h, ctypes.c_int]),
     "pyr_dg_set_tensor_traces": (ctypes.c_int, [_c_h, ctypes.c_int]),
+    "pyr_dg_get_tensor_traces": (ctypes.c_int, [_c_h, ctypes.POINTER(ctypes.c_int)]),
     "pyr_dg_batch_launch_mode": (ctypes.c_int, [_c_h, _c_ip, _c_ip]),
     "pyr_dg_batch_set_launch_mode": (ctypes.c_int, [_c_h, ctypes.c_int]),
 }
@@ -338,6 +339,13 @@ class Solver:
         the state, 8 elements x 4 fields per tile, FP64-accurate, instead of the FP64 trace
         kernel."""
         _check(lib().pyr_dg_set_tensor_traces(self._h, 1 if enable else 0))
+
+    @property
+    def tensor_traces(self):
+        """Whether stepping computes the face traces on the tensor cores (see set_tensor_traces)."""
+        v = ctypes.c_int()
+        _check(lib().pyr_dg_get_tensor_traces(self._h, ctypes.byref(v)))
+        return bool(v.value)
 
     def set_error_cache(self, enable=True):
         """Store the exact fields' spatial factors for error() when they fit (the default),

@@ -1063,6 +1063,12 @@ int pyr_dg_set_tensor_traces(pyr_dg* h, int enable) {
   return enable_tensor_traces(h);
 }
 
+int pyr_dg_get_tensor_traces(const pyr_dg* h, int* enabled) {
+  if (!h || !enabled) return fail(PYR_DG_ERR_BAD_ARG, "null argument");
+  *enabled = h->use_tctr ? 1 : 0;
+  return PYR_DG_OK;
+}
+
 int pyr_dg_profile(pyr_dg* h, int enable) {
   if (!h) return fail(PYR_DG_ERR_BAD_ARG, "null handle");
   DeviceGuard g(h->device);

@@ -187,7 +187,8 @@ def test_state_roundtrip_host_and_device(torch_cuda):
 
 
 def test_full_size_config2_sampled(torch_cuda):
-    """Config of the benchmark: 32^3 hexes x 6 = 196,608 pyramids, +-0.05h (seed 1), N = 4, FP64.
+    """Config of the benchmark: 32^3 hexes x 6 = 196,608 pyramids, +-0.05h (seed 1), N = 4, FP64,
+    stepping with the face traces on the tensor cores (the handle's default at this size).
 
     (1) rhs of a random state, checked on sampled elements: the oracle runs on
     the sample's face neighbourhood; (2) one LSRK4 step from the projected
@@ -202,6 +203,7 @@ def test_full_size_config2_sampled(torch_cuda):
     samples = [int(x) for x in rng.choice(K, 3, replace=False)] + [0, K - 1]
     U = random_state(K, 55, 12)
     with _solver(v, e, N) as s:
+        assert s.tensor_traces  # the stepping path the bench times: FP64 traces on the tensor cores
         R = s.rhs(torch.tensor(U, device="cuda")).cpu().numpy()
         dt_or = PyramidDG(v, e[:6], N).dt_cfl(0.5)  # a fixed dt from one hex's pyramids
         s.project(0.0)
