@@ -128,12 +128,22 @@ EX64_HD double ex64_combine(const int32_t G[8], int Z) {
 // The same sum to FP64 through floor(V / 2^8), which fits in 63 bits when |G_0| < 2^21 (K <= 127
 // terms) and |G_s| < 2^22: one 64-bit integer, rounded once to nearest (ties to even) and scaled
 // by 2^(Z+8). The result is within 2^(Z+8) plus half an ulp of V 2^Z, below the truncation of
-// the dropped levels for K >= 1 (2^(Z+8) = 2^-55 of the scale 2^(E+F-2044)); about half the
-// integer operations of ex64_combine.
+// the dropped levels for K >= 1 (2^(Z+8) = 2^-55 of the scale 2^(E+F-2044)). On the device the
+// integer-to-FP64 conversion instruction normalises and rounds (the same round to nearest, ties
+// to even, of the same integer) and the scale is added to its exponent field; the host spells
+// the normalisation and rounding out, with the same results.
 EX64_HD double ex64_combine_fast(const int32_t G[8], int Z) {
   const int64_t v = (int64_t)G[0] * (1ll << 41) + (int64_t)G[1] * (1ll << 34) + (int64_t)G[2] * (1ll << 27) +
                     (int64_t)G[3] * (1ll << 20) + (int64_t)G[4] * (1ll << 13) + (int64_t)G[5] * 64 +
                     (((int64_t)G[6] * 128 + G[7]) >> 8);
+#if defined(__CUDA_ARCH__)
+  if (v == 0) return 0.0;
+  const uint64_t b = (uint64_t)__double_as_longlong(__ll2double_rn(v));
+  const int bexp = (int)((b >> 52) & 0x7FF) + Z + 8;
+  if (bexp <= 0) return 0.0;
+  if (bexp >= 2047) return ex64_from_bits((b & (1ull << 63)) | (0x7FFull << 52));
+  return ex64_from_bits(b + ((uint64_t)(int64_t)(Z + 8) << 52));
+#else
   const uint64_t sgn = (uint64_t)(v >> 63);  // 0 or all ones
   uint64_t m = ((uint64_t)v ^ sgn) - sgn;    // |v|
   if (m == 0) return 0.0;
@@ -147,6 +157,7 @@ EX64_HD double ex64_combine_fast(const int32_t G[8], int Z) {
   if (bexp >= 2047) return ex64_from_bits((sgn << 63) | (0x7FFull << 52));
   // the leading one adds 1 to the exponent field; a rounding carry to 2^53 adds one more
   return ex64_from_bits((sgn << 63) | (((uint64_t)(bexp - 1) << 52) + mant));
+#endif
 }
 
 #if defined(__cplusplus)
