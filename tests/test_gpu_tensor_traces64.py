@@ -58,7 +58,7 @@ def test_fp64_tensor_traces_match_oracle_and_trace_kernel(torch_cuda, N):
     assert _rel(tc, cc) <= TOL_PATHS
 
 
-@pytest.mark.parametrize("N", [2, 4])
+@pytest.mark.parametrize("N", [2, 3, 4])
 def test_fp64_tensor_traces_several_tiles_per_cta(torch_cuda, N):
     """11^3 hexes = 7986 pyramids = 998 full tiles and one of 2 elements over one CTA per SM
     (the persistent loop, both accumulators and state slots, the exponent ring); 10 steps."""
