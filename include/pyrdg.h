@@ -268,13 +268,14 @@ int pyr_dg_set_tensor_mixing(pyr_dg* h, int enable);
  *    elements with FP64 accuracy: Phi_f's rows and the state's rows are cut into 8 exact
  *    balanced base-128 digits against each row's largest exponent (BF16 operands of
  *    tcgen05.mma kind::f16), the 36 digit products of each level s = i + j <= 7 are summed
- *    exactly as integers below 2^22 in FP32 accumulators, and integer arithmetic recombines
- *    the 8 levels into FP64. Each trace is within 15.1 K 2^-58 + 2^-55 of 2^(E+F-2044) (E, F:
+ *    exactly as integers below 2^22 in FP32 accumulators, and integer arithmetic with one
+ *    integer-to-FP64 conversion recombines the 8 levels into FP64. Each trace is within
+ *    15.1 K 2^-58 + 2^-55 of 2^(E+F-2044) (E, F:
  *    the two rows' largest biased exponents, K = Np terms) plus half an ulp of the exact dot
  *    product, below FP64's own worst-case rounding bound for such a sum. It replaces the FP64
  *    trace kernel before each fused stage; pyr_dg_rhs and the projection keep that kernel.
- *    Handles of at least 40,000 elements start with it where it measured faster (N = 4). The
- *    operator takes 16 * 128 * Np(padded to 16) bytes.
+ *    Handles of at least 40,000 elements start with it at N = 3, 4, where it measured
+ *    faster (a tie at N = 2). The operator takes 16 * 128 * Np(padded to 16) + 512 bytes.
  * enable != 0 selects these traces, 0 the CUDA-core paths. Other handles (advection, the nodal
  * basis, FP64 at N = 1 or N >= 5) return PYR_DG_ERR_BAD_ARG. Completion waits are bounded as
  * for pyr_dg_set_tensor_mixing. */
