@@ -4,9 +4,9 @@
 // balanced BF16 digits against a per-row exponent (exact64.h): Phi_f's rows (face points) once
 // on the host, the state's rows (element-field pairs) per tile here. The level sums
 // G_s = sum_{i+j=s} a_i b_j^T, s = 0..7, are integers below 2^22, exact in FP32 accumulators, and
-// the epilogue recombines them with integer operations into an FP64 value of sum_s G_s 2^(-7s)
-// times the two rows' scales (ex64_combine_fast: within 2^-55 of the scales' product plus half
-// an ulp).
+// the epilogue recombines them (integer operations and one integer-to-FP64 conversion) into an
+// FP64 value of sum_s G_s 2^(-7s) times the two rows' scales (ex64_combine_fast: within 2^-55
+// of the scales' product plus half an ulp).
 //  - tcgen05.mma kind::f16 (BF16 operands, FP32 accumulation in TMEM), M = 128 face points
 //    (Nfc <= 128 for N <= 4), K = the Np modes padded to 16, 32 state rows per tile (8 elements
 //    x 4 fields, the state's own row order). The accumulator of a tile is 8 levels x 32 columns;
@@ -16,7 +16,7 @@
 //  - the operator's 8 slices stay in shared memory for the CTA's lifetime (8 x 128 x KP BF16);
 //    the state is sliced into two alternating slots (8 x 32 x KP BF16), both in the K-major
 //    no-swizzle operand layout (core matrices of 8 rows x 8 BF16).
-//  - warp-specialised persistent CTAs: 4 producer warps (from warp 8) load the next tile while
+//  - warp-specialised persistent CTAs: 4 producer warps (from warp EW) load the next tile while
 //    they slice the current one (lane l of producer warp w takes state row 8 w + l % 8 and mode
 //    groups l / 8 + 4 t of 8 modes, so that each 8-lane phase of a slice store fills one core
 //    matrix); the row's exponent is a maximum over the 4 lanes that hold the row; thread 0 of
